@@ -1,0 +1,171 @@
+/*
+ * lrbatch.h -- C ABI of a GB300 (sm_103a) library for batched small and
+ * rectangular FP64 matrix multiplication, C_i += A_i * B_i.
+ *
+ * The operation is the batched multiplication of low-rank blocks of
+ * Deshmukh, Yokota and Bosilca, "Cache Optimization and Performance Modeling
+ * of Batched, Small, and Rectangular Matrix Multiplication on Intel, AMD, and
+ * Fujitsu Processors" (arXiv 2311.07602):
+ *   - a block of shape (m, n, rank) is stored as U S V (Eq. 1, Sec. 3);
+ *   - the low-rank product multiplies a "skinny" and a "small" matrix
+ *     (Alg. 1; first step C_temp = A_{V^T} B_U), batched over many
+ *     independent blocks (Alg. 2, loop 1 over the batch);
+ *   - all arithmetic is IEEE binary64 (Sec. 7).
+ * Two shapes dominate: the tall-skinny T-form C(b x r) += A(b x b) B(b x r)
+ * and the outer O-form C(b x b) += A(b x r) B(r x b); any m, n, k >= 1 is
+ * accepted.
+ *
+ * Conventions for every call:
+ *   - Matrices are column-major: element (i, j) of X is X[i + j*ldx].
+ *   - Operand pointers in lrb_gemm_desc are DEVICE pointers on the handle's
+ *     GPU; descriptor arrays passed to the library are HOST arrays that the
+ *     library copies (the caller may free them when the call returns).
+ *   - `stream` arguments are cudaStream_t values passed as void* (NULL = the
+ *     legacy default stream).
+ *   - No call aborts, throws or traps.  Failures return a status code and
+ *     set a per-thread message readable with lrb_last_error().  Invalid
+ *     arguments are rejected before any CUDA call is made.
+ */
+#ifndef LRBATCH_H
+#define LRBATCH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lrb_status {
+    LRB_OK = 0,
+    LRB_ERR_INVALID = 1,      /* bad argument: null pointer, dim <= 0, ld < rows, size overflow */
+    LRB_ERR_ALIAS = 2,        /* a C range overlaps another C or any A/B range */
+    LRB_ERR_NOMEM = 3,        /* device or host allocation failed */
+    LRB_ERR_BUDGET = 4,       /* a request alone exceeds the queue's HBM budget */
+    LRB_ERR_QUEUE_FULL = 5,   /* back-pressure: too many requests waiting */
+    LRB_ERR_TIMEOUT = 6,      /* a bounded wait ran out */
+    LRB_ERR_DEVICE = 7,       /* a CUDA call failed */
+    LRB_ERR_UNSUPPORTED = 8   /* valid request this build cannot serve */
+} lrb_status;
+
+/* One batch entry: C(m x n) += A(m x k) * B(k x n), binary64, column-major,
+ * device pointers.  lda >= m, ldb >= k, ldc >= m.  C must not overlap A, B or
+ * the C of another entry (A and B may be shared between entries).
+ * T-form: m = b, n = r, k = b.  O-form: m = n = b, k = r. */
+typedef struct lrb_gemm_desc {
+    const double* A;
+    const double* B;
+    double* C;
+    int32_t m, n, k;
+    int32_t lda, ldb, ldc;
+} lrb_gemm_desc;
+
+/* Arithmetic of a plan.  FP64: binary64 FMAs (DFMA pipe).  FP64_DMMA_ALLOWED:
+ * binary64, and the autotuner may also pick FP64 tensor-core (DMMA) tiles.
+ * SPLIT_*: the operands are cut into S BF16/FP16 digit slices per k-chunk,
+ * multiplied on the tensor cores with FP32 accumulation and recombined in
+ * binary64 (Ozaki-style splitting; not in the paper, which is FP64-only). */
+typedef enum lrb_precision {
+    LRB_PREC_FP64 = 0,
+    LRB_PREC_FP64_DMMA_ALLOWED = 1,
+    LRB_PREC_SPLIT_BF16_S3 = 2,
+    LRB_PREC_SPLIT_BF16_S4 = 3,
+    LRB_PREC_SPLIT_FP16_S3 = 4,
+    LRB_PREC_SPLIT_FP16_S4 = 5
+} lrb_precision;
+
+typedef struct lrb_plan_opts {
+    int32_t precision;      /* lrb_precision */
+    int32_t use_graph;      /* 1: lrb_launch replays a captured CUDA graph */
+    int32_t tune;           /* 1: time candidate tiles for unseen shape buckets; 0: heuristic */
+    int32_t force_variant;  /* >= 0: use this FP64 tile variant for every entry (testing) */
+    int32_t check_alias;    /* 1: reject overlapping C ranges (LRB_ERR_ALIAS) */
+    int32_t reserved[3];
+} lrb_plan_opts;
+
+typedef struct lrb_handle lrb_handle;
+typedef struct lrb_plan lrb_plan;
+typedef struct lrb_queue lrb_queue;
+
+/* Plan summary. */
+typedef struct lrb_plan_info {
+    int64_t entries;
+    int64_t items;          /* output tiles in the device work list */
+    int64_t groups;         /* distinct (variant, m, n, k) groups = launches of lrb_launch_plain */
+    double flops;           /* sum of 2 m n k */
+    double alg_bytes;       /* sum of 8 (m k + k n + 2 m n): each operand once, C read and written */
+    int32_t grid;           /* CTAs of the persistent launch */
+    int32_t precision;
+} lrb_plan_info;
+
+/* ---- handle -------------------------------------------------------------
+ * Selects `device` (a CUDA ordinal), loads the tile-tuning cache (path from
+ * $LRB_TUNE_CACHE, else none) and owns the streams and scratch it creates.
+ * lrb_destroy frees them; it synchronises the device first. */
+lrb_status lrb_create(lrb_handle** out, int device);
+lrb_status lrb_destroy(lrb_handle* h);
+
+/* ---- plans --------------------------------------------------------------
+ * lrb_plan_create copies `count` host descriptors, validates them (the checks of
+ * lrb_validate), picks a tile variant per entry (autotuned per shape bucket,
+ * cached in the handle), splits every entry into output tiles, orders the
+ * tiles longest-first and uploads descriptors and tiles to plan-owned device
+ * memory.  opts == NULL means {FP64, no graph, tune, no force, check alias}.
+ * The operand buffers are not touched until a launch. */
+lrb_status lrb_plan_create(lrb_handle* h, const lrb_gemm_desc* host_descs, size_t count,
+                           const lrb_plan_opts* opts, lrb_plan** out);
+
+/* Enqueue the whole batch as ONE persistent launch on `stream`: a CTA per SM
+ * slot pulls tiles from a device work counter until the list is empty (the
+ * counter reset and the kernel are one captured graph when use_graph = 1).
+ * Asynchronous; A, B, C must stay valid until the stream passes this point.
+ * Re-launching a plan repeats C += A B. */
+lrb_status lrb_launch(lrb_plan* p, void* stream);
+
+/* The comparator: one uniform-grid launch per distinct (variant, m, n, k)
+ * group, same tile code, hence bitwise the same results as lrb_launch. */
+lrb_status lrb_launch_plain(lrb_plan* p, void* stream);
+
+lrb_status lrb_plan_get_info(const lrb_plan* p, lrb_plan_info* info);
+
+/* Frees the plan's device memory after synchronising its last stream. */
+lrb_status lrb_plan_destroy(lrb_plan* p);
+
+/* Host-buffer form of a whole batch: the descriptors' A, B and C are HOST
+ * pointers (pinned memory gives full copy speed; pageable works).  Copies
+ * A, B and C into a handle-owned device arena (entries packed with tight
+ * leading dimensions; runs of host-contiguous tight entries move in one copy;
+ * an operand whose pointer and shape repeat an earlier entry's is copied
+ * once), runs the batch as one persistent launch (the plan is cached and
+ * reused while the shape list repeats), copies every C back and synchronises
+ * `stream`.  Returns after host C holds the result.  Not thread-safe per
+ * handle; the arena grows to the largest batch seen and is freed by
+ * lrb_destroy. */
+lrb_status lrb_execute_host(lrb_handle* h, const lrb_gemm_desc* host_descs, size_t count,
+                            const lrb_plan_opts* opts, void* stream);
+
+/* Host-only: the argument checks lrb_plan_create performs, without a GPU.
+ * LRB_ERR_INVALID for null pointers, count == 0, m/n/k <= 0, ld < rows,
+ * element extents that overflow int64, count above 2^31 - 1;
+ * LRB_ERR_ALIAS when opts->check_alias and a C range overlaps another C or
+ * any A/B range (byte ranges from first to last element). */
+lrb_status lrb_validate(const lrb_gemm_desc* host_descs, size_t count, const lrb_plan_opts* opts);
+
+/* Host-only tile list of the planner for forced variant `variant`: writes up
+ * to `cap` items as (entry, row0, col0, rows, cols) int32 quintuples in
+ * launch order and returns their number in *n_items (for tests of the
+ * scheduler invariant: every output element in exactly one tile). */
+lrb_status lrb_plan_tiles_host(const lrb_gemm_desc* host_descs, size_t count, int32_t variant,
+                               int32_t* out, size_t cap, size_t* n_items);
+
+/* Number of FP64 tile variants and their tile extents (rows x cols). */
+int32_t lrb_variant_count(void);
+lrb_status lrb_variant_shape(int32_t variant, int32_t* bm, int32_t* bn, int32_t* is_dmma);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* lrb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LRBATCH_H */

@@ -1,0 +1,808 @@
+// C ABI: handles, argument validation, the planner (tiles, longest-first
+// order, plain-launch groups), the tile autotuner and CUDA-graph capture.
+//
+// The batch is a list of independent entries, as in the paper's batched
+// low-rank multiplication (Alg. 2, loop 1 runs over independent blocks).  On
+// the CPU the paper splits that loop across cores and packs operands into
+// caches (Alg. 3); here every entry is cut into output tiles and one
+// persistent kernel pulls tiles from a device-side counter, largest first.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <new>
+#include <sstream>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "lrb_internal.h"
+#include "split.h"
+
+using namespace lrb;
+
+namespace {
+
+thread_local std::string g_err;
+
+lrb_status fail(lrb_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+lrb_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(LRB_ERR_DEVICE, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define LRB_CUDA(call)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+lrb_plan_opts default_opts() {
+    lrb_plan_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.precision = LRB_PREC_FP64;
+    o.use_graph = 0;
+    o.tune = 1;
+    o.force_variant = -1;
+    o.check_alias = 1;
+    return o;
+}
+
+// Byte range [lo, hi) covered by a column-major rows x cols matrix.
+struct Range {
+    uint64_t lo, hi;
+    int64_t entry;
+};
+
+bool extent(const void* p, int32_t rows, int32_t cols, int32_t ld, Range* r) {
+    // last element index = ld * (cols - 1) + rows - 1, all non-negative here
+    const __int128 last = (__int128)ld * (cols - 1) + rows - 1;
+    const __int128 bytes = (last + 1) * 8;
+    const __int128 lo = (__int128)(uintptr_t)p;
+    if (bytes > ((__int128)1 << 62) || lo + bytes > ((__int128)1 << 64) - 1) return false;
+    r->lo = (uint64_t)lo;
+    r->hi = (uint64_t)(lo + bytes);
+    return true;
+}
+
+lrb_status validate(const lrb_gemm_desc* d, size_t count, const lrb_plan_opts& o) {
+    if (!d) return fail(LRB_ERR_INVALID, "host_descs is NULL");
+    if (count == 0) return fail(LRB_ERR_INVALID, "count is 0");
+    if (count > 0x7fffffffull) return fail(LRB_ERR_INVALID, "count exceeds 2^31-1");
+    if (o.precision < LRB_PREC_FP64 || o.precision > LRB_PREC_SPLIT_FP16_S4)
+        return fail(LRB_ERR_INVALID, "unknown precision");
+    if (o.force_variant >= kNumVariants) return fail(LRB_ERR_INVALID, "force_variant out of range");
+    std::vector<Range> cr, ab;
+    if (o.check_alias) {
+        cr.reserve(count);
+        ab.reserve(2 * count);
+    }
+    for (size_t e = 0; e < count; ++e) {
+        const lrb_gemm_desc& x = d[e];
+        char buf[160];
+        if (!x.A || !x.B || !x.C) {
+            std::snprintf(buf, sizeof buf, "entry %zu: NULL operand pointer", e);
+            return fail(LRB_ERR_INVALID, buf);
+        }
+        if (((uintptr_t)x.A | (uintptr_t)x.B | (uintptr_t)x.C) & 7u) {
+            std::snprintf(buf, sizeof buf, "entry %zu: operand pointer not 8-byte aligned", e);
+            return fail(LRB_ERR_INVALID, buf);
+        }
+        if (x.m <= 0 || x.n <= 0 || x.k <= 0) {
+            std::snprintf(buf, sizeof buf, "entry %zu: m, n, k must be >= 1 (got %d, %d, %d)", e, x.m, x.n, x.k);
+            return fail(LRB_ERR_INVALID, buf);
+        }
+        if (x.lda < x.m || x.ldb < x.k || x.ldc < x.m) {
+            std::snprintf(buf, sizeof buf, "entry %zu: leading dimension below rows (lda %d, ldb %d, ldc %d)", e,
+                          x.lda, x.ldb, x.ldc);
+            return fail(LRB_ERR_INVALID, buf);
+        }
+        Range ra, rb, rc;
+        if (!extent(x.A, x.m, x.k, x.lda, &ra) || !extent(x.B, x.k, x.n, x.ldb, &rb) ||
+            !extent(x.C, x.m, x.n, x.ldc, &rc)) {
+            std::snprintf(buf, sizeof buf, "entry %zu: operand extent overflows", e);
+            return fail(LRB_ERR_INVALID, buf);
+        }
+        if (o.check_alias) {
+            ra.entry = rb.entry = rc.entry = (int64_t)e;
+            cr.push_back(rc);
+            ab.push_back(ra);
+            ab.push_back(rb);
+        }
+    }
+    if (o.check_alias) {
+        std::sort(cr.begin(), cr.end(), [](const Range& a, const Range& b) { return a.lo < b.lo; });
+        for (size_t i = 1; i < cr.size(); ++i)
+            if (cr[i].lo < cr[i - 1].hi) {
+                char buf[160];
+                std::snprintf(buf, sizeof buf, "C of entries %lld and %lld overlap", (long long)cr[i - 1].entry,
+                              (long long)cr[i].entry);
+                return fail(LRB_ERR_ALIAS, buf);
+            }
+        for (const Range& r : ab) {
+            // first C range whose end is beyond r.lo
+            auto it = std::upper_bound(cr.begin(), cr.end(), r.lo,
+                                       [](uint64_t v, const Range& c) { return v < c.hi; });
+            if (it != cr.end() && it->lo < r.hi) {
+                char buf[160];
+                std::snprintf(buf, sizeof buf, "an operand of entry %lld overlaps C of entry %lld",
+                              (long long)r.entry, (long long)it->entry);
+                return fail(LRB_ERR_ALIAS, buf);
+            }
+        }
+    }
+    return LRB_OK;
+}
+
+int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// Issued multiply-adds of one tile (rows rounded up to whole 32-row slots,
+// DMMA fragments rounded to 8), the planner's cost for longest-first order.
+double tile_cost(const Variant& V, int h, int w, int k) {
+    if (V.dmma) return (double)(ceil_div(h, 8) * 8) * (ceil_div(w, 8) * 8) * (ceil_div(k, 4) * 4);
+    return (double)(ceil_div(h, 32) * 32) * w * k;
+}
+
+struct Group {
+    int variant, m, n, k, tiles_m, tiles_n;
+    int offset, count;
+};
+
+void make_tiles(const lrb_gemm_desc* d, size_t count, const std::vector<int>& var, std::vector<Item>& items) {
+    struct Keyed {
+        double cost;
+        Item it;
+    };
+    std::vector<Keyed> tmp;
+    for (size_t e = 0; e < count; ++e) {
+        const Variant& V = kVariants[var[e]];
+        const int bm = V.bm(), bn = V.bn();
+        for (int c0 = 0; c0 < d[e].n; c0 += bn)
+            for (int r0 = 0; r0 < d[e].m; r0 += bm) {
+                const int h = std::min(bm, d[e].m - r0), w = std::min(bn, d[e].n - c0);
+                tmp.push_back({tile_cost(V, h, w, d[e].k), Item{(int32_t)e, r0, c0, var[e]}});
+            }
+    }
+    std::stable_sort(tmp.begin(), tmp.end(), [](const Keyed& a, const Keyed& b) { return a.cost > b.cost; });
+    items.resize(tmp.size());
+    for (size_t i = 0; i < tmp.size(); ++i) items[i] = tmp[i].it;
+}
+
+int bucket(int x) { return (int)std::floor(2.0 * std::log2((double)x) + 1e-9); }
+int bucket_center(int b) { return std::max(1, (int)std::lround(std::pow(2.0, (b + 0.5) / 2.0))); }
+
+int heuristic_variant(int m, int n, int k, bool dmma_ok) {
+    (void)m;
+    (void)k;
+    (void)dmma_ok;
+    if (n <= 8) return 0;
+    if (n <= 16) return 1;
+    if (n <= 32) return 2;
+    return 3;
+}
+
+}  // namespace
+
+struct lrb_handle {
+    int device = 0;
+    int sms = 0;
+    int blocks_per_sm = 0;
+    std::string gpu_key;
+    std::string cache_path;
+    std::map<std::string, int> tuned;
+    std::mutex mu;
+    cudaStream_t stream = nullptr;   // tuning and graph capture
+    void* scratch = nullptr;          // tuning buffers
+    size_t scratch_bytes = 0;
+    // lrb_execute_host: device arena and the plan cached for the last shape list
+    void* arena = nullptr;
+    size_t arena_bytes = 0;
+    std::vector<lrb_gemm_desc> host_key;
+    lrb_plan_opts host_opts{};
+    lrb_plan* host_plan = nullptr;
+};
+
+struct lrb_plan {
+    lrb_handle* h = nullptr;
+    int precision = LRB_PREC_FP64;
+    std::vector<lrb_gemm_desc> descs;
+    void* dmem = nullptr;
+    DevDesc* d_descs = nullptr;
+    Item* d_items = nullptr;
+    int32_t* d_group_entries = nullptr;
+    int* d_head = nullptr;
+    int n_items = 0;
+    int grid = 0;
+    std::vector<Group> groups;
+    bool use_graph = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t last_stream = nullptr;
+    bool launched = false;
+    lrb_plan_info info{};
+    split::SplitPlan* sp = nullptr;
+};
+
+namespace {
+
+std::string bucket_key(int m, int n, int k, bool dmma_ok) {
+    char buf[64];
+    std::snprintf(buf, sizeof buf, "m%d_n%d_k%d_%s", bucket(m), bucket(n), bucket(k), dmma_ok ? "dmma" : "dfma");
+    return buf;
+}
+
+void load_cache(lrb_handle* h) {
+    if (h->cache_path.empty()) return;
+    std::ifstream f(h->cache_path);
+    if (!f) return;
+    std::stringstream ss;
+    ss << f.rdbuf();
+    const std::string s = ss.str();
+    // {"gpu": "<key>", "buckets": {"<bucket>": <variant>, ...}}
+    const std::string gk = "\"gpu\": \"" + h->gpu_key + "\"";
+    if (s.find(gk) == std::string::npos) return;   // another GPU / driver / version: ignore
+    size_t p = s.find("\"buckets\"");
+    if (p == std::string::npos) return;
+    p = s.find('{', p);
+    while (p != std::string::npos) {
+        size_t q0 = s.find('"', p + 1);
+        if (q0 == std::string::npos) break;
+        size_t q1 = s.find('"', q0 + 1);
+        if (q1 == std::string::npos) break;
+        size_t c = s.find(':', q1);
+        if (c == std::string::npos) break;
+        const int v = std::atoi(s.c_str() + c + 1);
+        if (v >= 0 && v < kNumVariants) h->tuned[s.substr(q0 + 1, q1 - q0 - 1)] = v;
+        p = s.find(',', c);
+    }
+}
+
+void save_cache(lrb_handle* h) {
+    if (h->cache_path.empty()) return;
+    const std::string tmp = h->cache_path + ".tmp";
+    {
+        std::ofstream f(tmp);
+        if (!f) return;
+        f << "{\"gpu\": \"" << h->gpu_key << "\", \"buckets\": {";
+        bool first = true;
+        for (auto& kv : h->tuned) {
+            f << (first ? "" : ", ") << "\"" << kv.first << "\": " << kv.second;
+            first = false;
+        }
+        f << "}}\n";
+    }
+    std::rename(tmp.c_str(), h->cache_path.c_str());
+}
+
+// Time each candidate variant on a uniform batch of the bucket's central
+// shape (plain launches, 2 repetitions after a warm-up) and keep the fastest.
+lrb_status tune_bucket(lrb_handle* h, int m, int n, int k, bool dmma_ok, int* best) {
+    const int M = bucket_center(bucket(m)), N = bucket_center(bucket(n)), K = bucket_center(bucket(k));
+    const double flops_entry = 2.0 * M * N * K;
+    const double bytes_entry = 8.0 * ((double)M * K + (double)K * N + (double)M * N);
+    int E = (int)std::ceil(3e9 / flops_entry);
+    E = std::max(1, std::min(E, (int)(512e6 / bytes_entry)));
+    E = std::max(E, 1);
+    const size_t need = (size_t)(bytes_entry * E) + 4096 + (size_t)E * (sizeof(DevDesc) + 4);
+    if (need > h->scratch_bytes) {
+        if (h->scratch) cudaFree(h->scratch);
+        h->scratch = nullptr;
+        h->scratch_bytes = 0;
+        LRB_CUDA(cudaMalloc(&h->scratch, need));
+        h->scratch_bytes = need;
+    }
+    char* base = (char*)h->scratch;
+    LRB_CUDA(cudaMemsetAsync(base, 0, need, h->stream));
+    std::vector<DevDesc> dd(E);
+    std::vector<int32_t> ent(E);
+    double* A = (double*)base;
+    double* B = A + (size_t)M * K * E;
+    double* C = B + (size_t)K * N * E;
+    for (int e = 0; e < E; ++e) {
+        dd[e] = DevDesc{A + (size_t)M * K * e, B + (size_t)K * N * e, C + (size_t)M * N * e, M, N, K, M, K, M};
+        ent[e] = e;
+    }
+    char* tail = (char*)(C + (size_t)M * N * E);
+    tail = (char*)(((uintptr_t)tail + 255) & ~(uintptr_t)255);
+    DevDesc* d_dd = (DevDesc*)tail;
+    int32_t* d_ent = (int32_t*)(tail + sizeof(DevDesc) * E);
+    LRB_CUDA(cudaMemcpyAsync(d_dd, dd.data(), sizeof(DevDesc) * E, cudaMemcpyHostToDevice, h->stream));
+    LRB_CUDA(cudaMemcpyAsync(d_ent, ent.data(), sizeof(int32_t) * E, cudaMemcpyHostToDevice, h->stream));
+    cudaEvent_t e0, e1;
+    LRB_CUDA(cudaEventCreate(&e0));
+    LRB_CUDA(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    *best = heuristic_variant(m, n, k, dmma_ok);
+    for (int v = 0; v < kNumVariants; ++v) {
+        const Variant& V = kVariants[v];
+        if (V.dmma && !dmma_ok) continue;
+        // skip tiles more than twice as tall/wide as the shape needs
+        if (V.bm() > 32 && V.bm() >= 2 * std::max(M, 32)) continue;
+        if (V.bn() > 8 && V.bn() >= 2 * std::max(N, 8)) continue;
+        const int tm = ceil_div(M, V.bm()), tn = ceil_div(N, V.bn());
+        cudaError_t ce = launch_plain_group(v, d_dd, d_ent, E, tm, tn, h->stream);
+        if (ce != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_fail(ce, "tuning launch");
+        }
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            cudaEventRecord(e0, h->stream);
+            launch_plain_group(v, d_dd, d_ent, E, tm, tn, h->stream);
+            cudaEventRecord(e1, h->stream);
+            ce = cudaEventSynchronize(e1);
+            if (ce != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return cuda_fail(ce, "tuning run");
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms_min = std::min(ms_min, ms);
+        }
+        if (ms_min < best_ms) {
+            best_ms = ms_min;
+            *best = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return LRB_OK;
+}
+
+lrb_status choose_variants(lrb_handle* h, const lrb_gemm_desc* d, size_t count, const lrb_plan_opts& o,
+                           std::vector<int>& var) {
+    var.resize(count);
+    const bool dmma_ok = o.precision == LRB_PREC_FP64_DMMA_ALLOWED;
+    std::lock_guard<std::mutex> lock(h->mu);
+    bool dirty = false;
+    std::map<std::string, int> local;
+    for (size_t e = 0; e < count; ++e) {
+        if (o.force_variant >= 0) {
+            var[e] = o.force_variant;
+            continue;
+        }
+        const std::string key = bucket_key(d[e].m, d[e].n, d[e].k, dmma_ok);
+        auto it = local.find(key);
+        if (it != local.end()) {
+            var[e] = it->second;
+            continue;
+        }
+        auto jt = h->tuned.find(key);
+        int v;
+        if (jt != h->tuned.end()) {
+            v = jt->second;
+        } else if (o.tune) {
+            lrb_status s = tune_bucket(h, d[e].m, d[e].n, d[e].k, dmma_ok, &v);
+            if (s != LRB_OK) return s;
+            h->tuned[key] = v;
+            dirty = true;
+        } else {
+            v = heuristic_variant(d[e].m, d[e].n, d[e].k, dmma_ok);
+        }
+        local[key] = v;
+        var[e] = v;
+    }
+    if (dirty) save_cache(h);
+    return LRB_OK;
+}
+
+void free_plan(lrb_plan* p) {
+    if (!p) return;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->sp) split::destroy(p->sp);
+    if (p->dmem) cudaFree(p->dmem);
+    delete p;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lrb_last_error(void) { return g_err.c_str(); }
+
+int32_t lrb_variant_count(void) { return kNumVariants; }
+
+lrb_status lrb_variant_shape(int32_t variant, int32_t* bm, int32_t* bn, int32_t* is_dmma) {
+    if (variant < 0 || variant >= kNumVariants) return fail(LRB_ERR_INVALID, "variant out of range");
+    if (bm) *bm = kVariants[variant].bm();
+    if (bn) *bn = kVariants[variant].bn();
+    if (is_dmma) *is_dmma = kVariants[variant].dmma;
+    return LRB_OK;
+}
+
+lrb_status lrb_validate(const lrb_gemm_desc* host_descs, size_t count, const lrb_plan_opts* opts) {
+    const lrb_plan_opts o = opts ? *opts : default_opts();
+    return validate(host_descs, count, o);
+}
+
+lrb_status lrb_plan_tiles_host(const lrb_gemm_desc* host_descs, size_t count, int32_t variant, int32_t* out,
+                               size_t cap, size_t* n_items) {
+    lrb_plan_opts o = default_opts();
+    o.check_alias = 0;
+    lrb_status s = validate(host_descs, count, o);
+    if (s != LRB_OK) return s;
+    if (variant < 0 || variant >= kNumVariants) return fail(LRB_ERR_INVALID, "variant out of range");
+    if (!n_items) return fail(LRB_ERR_INVALID, "n_items is NULL");
+    std::vector<int> var(count, variant);
+    std::vector<Item> items;
+    make_tiles(host_descs, count, var, items);
+    *n_items = items.size();
+    if (out) {
+        const Variant& V = kVariants[variant];
+        for (size_t i = 0; i < items.size() && i < cap; ++i) {
+            const lrb_gemm_desc& d = host_descs[items[i].entry];
+            out[5 * i + 0] = items[i].entry;
+            out[5 * i + 1] = items[i].row0;
+            out[5 * i + 2] = items[i].col0;
+            out[5 * i + 3] = std::min(V.bm(), d.m - items[i].row0);
+            out[5 * i + 4] = std::min(V.bn(), d.n - items[i].col0);
+        }
+    }
+    return LRB_OK;
+}
+
+lrb_status lrb_create(lrb_handle** out, int device) {
+    if (!out) return fail(LRB_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(LRB_ERR_INVALID, "device ordinal out of range");
+    LRB_CUDA(cudaSetDevice(device));
+    lrb_handle* h = new (std::nothrow) lrb_handle();
+    if (!h) return fail(LRB_ERR_NOMEM, "handle allocation");
+    h->device = device;
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "cudaGetDeviceProperties");
+    }
+    h->sms = prop.multiProcessorCount;
+    h->blocks_per_sm = persistent_blocks_per_sm();
+    if (h->blocks_per_sm <= 0) {
+        delete h;
+        return fail(LRB_ERR_DEVICE, "persistent kernel does not fit on this device");
+    }
+    int drv = 0;
+    cudaDriverGetVersion(&drv);
+    char key[256];
+    std::snprintf(key, sizeof key, "%s|cc%d%d|drv%d|lib1", prop.name, prop.major, prop.minor, drv);
+    h->gpu_key = key;
+    if (const char* p = std::getenv("LRB_TUNE_CACHE")) h->cache_path = p;
+    load_cache(h);
+    e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "cudaStreamCreate");
+    }
+    *out = h;
+    return LRB_OK;
+}
+
+lrb_status lrb_destroy(lrb_handle* h) {
+    if (!h) return fail(LRB_ERR_INVALID, "handle is NULL");
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    if (h->host_plan) free_plan(h->host_plan);
+    if (h->arena) cudaFree(h->arena);
+    if (h->scratch) cudaFree(h->scratch);
+    if (h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return LRB_OK;
+}
+
+lrb_status lrb_plan_create(lrb_handle* h, const lrb_gemm_desc* host_descs, size_t count, const lrb_plan_opts* opts,
+                           lrb_plan** out) {
+    if (!h) return fail(LRB_ERR_INVALID, "handle is NULL");
+    if (!out) return fail(LRB_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    const lrb_plan_opts o = opts ? *opts : default_opts();
+    lrb_status s = validate(host_descs, count, o);
+    if (s != LRB_OK) return s;
+    LRB_CUDA(cudaSetDevice(h->device));
+
+    lrb_plan* p = new (std::nothrow) lrb_plan();
+    if (!p) return fail(LRB_ERR_NOMEM, "plan allocation");
+    p->h = h;
+    p->precision = o.precision;
+    p->descs.assign(host_descs, host_descs + count);
+    double flops = 0, bytes = 0;
+    for (size_t e = 0; e < count; ++e) {
+        const double m = host_descs[e].m, n = host_descs[e].n, k = host_descs[e].k;
+        flops += 2 * m * n * k;
+        bytes += 8 * (m * k + k * n + 2 * m * n);
+    }
+    p->info.entries = (int64_t)count;
+    p->info.flops = flops;
+    p->info.alg_bytes = bytes;
+    p->info.precision = o.precision;
+
+    if (o.precision >= LRB_PREC_SPLIT_BF16_S3) {
+        s = split::create(h->device, h->sms, p->descs.data(), count, o.precision, &p->sp, &p->info);
+        if (s != LRB_OK) {
+            free_plan(p);
+            return s;
+        }
+        *out = p;
+        return LRB_OK;
+    }
+
+    std::vector<int> var;
+    s = choose_variants(h, host_descs, count, o, var);
+    if (s != LRB_OK) {
+        free_plan(p);
+        return s;
+    }
+    std::vector<Item> items;
+    make_tiles(host_descs, count, var, items);
+    if (items.size() > 0x7fffffffull) {
+        free_plan(p);
+        return fail(LRB_ERR_INVALID, "too many tiles");
+    }
+    // plain-launch groups: entries sharing (variant, m, n, k), in first-seen order
+    std::map<std::tuple<int, int, int, int>, int> gid;
+    std::vector<std::vector<int32_t>> members;
+    for (size_t e = 0; e < count; ++e) {
+        auto key = std::make_tuple(var[e], host_descs[e].m, host_descs[e].n, host_descs[e].k);
+        auto it = gid.find(key);
+        int g;
+        if (it == gid.end()) {
+            g = (int)members.size();
+            gid[key] = g;
+            members.emplace_back();
+            const Variant& V = kVariants[var[e]];
+            p->groups.push_back(Group{var[e], host_descs[e].m, host_descs[e].n, host_descs[e].k,
+                                      ceil_div(host_descs[e].m, V.bm()), ceil_div(host_descs[e].n, V.bn()), 0, 0});
+        } else {
+            g = it->second;
+        }
+        members[g].push_back((int32_t)e);
+    }
+    std::vector<int32_t> flat;
+    flat.reserve(count);
+    for (size_t g = 0; g < members.size(); ++g) {
+        p->groups[g].offset = (int)flat.size();
+        p->groups[g].count = (int)members[g].size();
+        flat.insert(flat.end(), members[g].begin(), members[g].end());
+    }
+
+    // one device allocation: descriptors | items | group entries | counter
+    auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t o_desc = 0;
+    const size_t o_items = align(o_desc + sizeof(DevDesc) * count);
+    const size_t o_grp = align(o_items + sizeof(Item) * std::max<size_t>(items.size(), 1));
+    const size_t o_head = align(o_grp + sizeof(int32_t) * count);
+    const size_t total = o_head + 256;
+    cudaError_t ce = cudaMalloc(&p->dmem, total);
+    if (ce != cudaSuccess) {
+        free_plan(p);
+        return fail(LRB_ERR_NOMEM, std::string("plan device memory: ") + cudaGetErrorString(ce));
+    }
+    char* base = (char*)p->dmem;
+    p->d_descs = (DevDesc*)(base + o_desc);
+    p->d_items = (Item*)(base + o_items);
+    p->d_group_entries = (int32_t*)(base + o_grp);
+    p->d_head = (int*)(base + o_head);
+    p->n_items = (int)items.size();
+    ce = cudaMemcpy(p->d_descs, host_descs, sizeof(DevDesc) * count, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess && !items.empty())
+        ce = cudaMemcpy(p->d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(p->d_group_entries, flat.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemset(p->d_head, 0, 256);
+    if (ce != cudaSuccess) {
+        free_plan(p);
+        return cuda_fail(ce, "plan upload");
+    }
+    p->grid = std::max(1, std::min(h->sms * h->blocks_per_sm, p->n_items));
+    p->info.items = p->n_items;
+    p->info.groups = (int64_t)p->groups.size();
+    p->info.grid = p->grid;
+
+    if (o.use_graph) {
+        cudaStream_t cs = h->stream;
+        ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (ce == cudaSuccess) {
+            cudaError_t le = launch_persistent(p->d_descs, p->d_items, p->n_items, p->d_head, p->grid, cs);
+            ce = cudaStreamEndCapture(cs, &p->graph);
+            if (le != cudaSuccess) ce = le;
+        }
+        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&p->exec, p->graph, 0);
+        if (ce != cudaSuccess) {
+            free_plan(p);
+            return cuda_fail(ce, "graph capture");
+        }
+        p->use_graph = true;
+    }
+    *out = p;
+    return LRB_OK;
+}
+
+lrb_status lrb_launch(lrb_plan* p, void* stream) {
+    if (!p) return fail(LRB_ERR_INVALID, "plan is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    LRB_CUDA(cudaSetDevice(p->h->device));
+    p->last_stream = s;
+    p->launched = true;
+    if (p->sp) {
+        cudaError_t e = split::launch(p->sp, s);
+        return e == cudaSuccess ? LRB_OK : cuda_fail(e, "split launch");
+    }
+    cudaError_t e = p->use_graph ? cudaGraphLaunch(p->exec, s)
+                                 : launch_persistent(p->d_descs, p->d_items, p->n_items, p->d_head, p->grid, s);
+    if (e != cudaSuccess) return cuda_fail(e, "persistent launch");
+    return LRB_OK;
+}
+
+lrb_status lrb_launch_plain(lrb_plan* p, void* stream) {
+    if (!p) return fail(LRB_ERR_INVALID, "plan is NULL");
+    if (p->sp) return fail(LRB_ERR_UNSUPPORTED, "split-precision plans have no plain launch");
+    cudaStream_t s = (cudaStream_t)stream;
+    LRB_CUDA(cudaSetDevice(p->h->device));
+    p->last_stream = s;
+    p->launched = true;
+    for (const Group& g : p->groups) {
+        cudaError_t e = launch_plain_group(g.variant, p->d_descs, p->d_group_entries + g.offset, g.count, g.tiles_m,
+                                           g.tiles_n, s);
+        if (e != cudaSuccess) return cuda_fail(e, "plain launch");
+    }
+    return LRB_OK;
+}
+
+lrb_status lrb_execute_host(lrb_handle* h, const lrb_gemm_desc* host_descs, size_t count, const lrb_plan_opts* opts,
+                            void* stream) {
+    if (!h) return fail(LRB_ERR_INVALID, "handle is NULL");
+    const lrb_plan_opts o = opts ? *opts : default_opts();
+    lrb_status st = validate(host_descs, count, o);
+    if (st != LRB_OK) return st;
+    LRB_CUDA(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+
+    // Device layout: A blocks, then B blocks, then C blocks, each packed with
+    // ld = rows.  An A or B block whose (pointer, rows, cols, ld) repeats an
+    // earlier one is shared.
+    struct Copy {
+        const double* host;
+        size_t dev;        // element offset in the arena
+        int rows, cols, ld;
+        size_t elems;      // contiguous run length (tight blocks)
+    };
+    std::vector<lrb_gemm_desc> dd(host_descs, host_descs + count);
+    std::vector<Copy> h2d, d2h;
+    size_t cursor = 0;
+    auto place = [&](int cls, std::vector<size_t>& where) {
+        std::map<std::tuple<uintptr_t, int, int, int>, size_t> seen;
+        where.resize(count);
+        const size_t cls_start = h2d.size();   // runs never merge across operand classes
+        for (size_t e = 0; e < count; ++e) {
+            const lrb_gemm_desc& x = host_descs[e];
+            const double* p = cls == 0 ? x.A : cls == 1 ? x.B : x.C;
+            const int rows = cls == 0 ? x.m : cls == 1 ? x.k : x.m;
+            const int cols = cls == 0 ? x.k : cls == 1 ? x.n : x.n;
+            const int ld = cls == 0 ? x.lda : cls == 1 ? x.ldb : x.ldc;
+            const auto key = std::make_tuple((uintptr_t)p, rows, cols, ld);
+            if (cls < 2) {
+                auto it = seen.find(key);
+                if (it != seen.end()) {
+                    where[e] = it->second;
+                    continue;
+                }
+            }
+            const size_t elems = (size_t)rows * cols;
+            where[e] = cursor;
+            if (cls < 2) seen[key] = cursor;
+            Copy c{p, cursor, rows, cols, ld, elems};
+            std::vector<Copy>& list = h2d;
+            if (list.size() > cls_start && ld == rows) {
+                Copy& b = list.back();
+                if (b.ld == b.rows && b.host + b.elems == p && b.dev + b.elems == cursor) {
+                    b.elems += elems;
+                    b.cols = -1;   // merged run: a 1-D copy
+                } else {
+                    list.push_back(c);
+                }
+            } else {
+                list.push_back(c);
+            }
+            cursor += elems;
+        }
+    };
+    std::vector<size_t> wa, wb, wc;
+    place(0, wa);
+    place(1, wb);
+    const size_t c_first = h2d.size();
+    place(2, wc);
+    d2h.assign(h2d.begin() + c_first, h2d.end());
+
+    const size_t need = cursor * 8 + 256;
+    if (need > h->arena_bytes) {
+        if (h->host_plan) {
+            free_plan(h->host_plan);
+            h->host_plan = nullptr;
+        }
+        cudaStreamSynchronize(s);
+        if (h->arena) cudaFree(h->arena);
+        h->arena = nullptr;
+        h->arena_bytes = 0;
+        cudaError_t ce = cudaMalloc(&h->arena, need);
+        if (ce != cudaSuccess) return fail(LRB_ERR_NOMEM, std::string("host-run arena: ") + cudaGetErrorString(ce));
+        h->arena_bytes = need;
+        h->host_key.clear();
+    }
+    double* base = (double*)h->arena;
+    for (size_t e = 0; e < count; ++e) {
+        dd[e].A = base + wa[e];
+        dd[e].B = base + wb[e];
+        dd[e].C = base + wc[e];
+        dd[e].lda = dd[e].m;
+        dd[e].ldb = dd[e].k;
+        dd[e].ldc = dd[e].m;
+    }
+    const bool same = h->host_plan && h->host_key.size() == count &&
+                      std::memcmp(h->host_key.data(), dd.data(), sizeof(lrb_gemm_desc) * count) == 0 &&
+                      std::memcmp(&h->host_opts, &o, sizeof(o)) == 0;
+    if (!same) {
+        if (h->host_plan) {
+            cudaStreamSynchronize(s);
+            free_plan(h->host_plan);
+            h->host_plan = nullptr;
+        }
+        lrb_plan* p = nullptr;
+        st = lrb_plan_create(h, dd.data(), count, &o, &p);
+        if (st != LRB_OK) return st;
+        h->host_plan = p;
+        h->host_key = dd;
+        h->host_opts = o;
+    }
+    auto copy = [&](const Copy& c, bool to_dev) -> cudaError_t {
+        double* dptr = base + c.dev;
+        if (c.cols < 0 || c.ld == c.rows) {
+            const size_t bytes = c.elems * 8;
+            return to_dev ? cudaMemcpyAsync(dptr, c.host, bytes, cudaMemcpyHostToDevice, s)
+                          : cudaMemcpyAsync((void*)c.host, dptr, bytes, cudaMemcpyDeviceToHost, s);
+        }
+        return to_dev ? cudaMemcpy2DAsync(dptr, (size_t)c.rows * 8, c.host, (size_t)c.ld * 8, (size_t)c.rows * 8,
+                                          c.cols, cudaMemcpyHostToDevice, s)
+                      : cudaMemcpy2DAsync((void*)c.host, (size_t)c.ld * 8, dptr, (size_t)c.rows * 8,
+                                          (size_t)c.rows * 8, c.cols, cudaMemcpyDeviceToHost, s);
+    };
+    for (const Copy& c : h2d) LRB_CUDA(copy(c, true));
+    st = lrb_launch(h->host_plan, stream);
+    if (st != LRB_OK) return st;
+    for (const Copy& c : d2h) LRB_CUDA(copy(c, false));
+    LRB_CUDA(cudaStreamSynchronize(s));
+    return LRB_OK;
+}
+
+lrb_status lrb_plan_get_info(const lrb_plan* p, lrb_plan_info* info) {
+    if (!p || !info) return fail(LRB_ERR_INVALID, "NULL argument");
+    *info = p->info;
+    return LRB_OK;
+}
+
+lrb_status lrb_plan_destroy(lrb_plan* p) {
+    if (!p) return fail(LRB_ERR_INVALID, "plan is NULL");
+    cudaSetDevice(p->h->device);
+    if (p->launched) {
+        cudaError_t e = p->last_stream ? cudaStreamSynchronize(p->last_stream) : cudaDeviceSynchronize();
+        if (e != cudaSuccess) {
+            free_plan(p);
+            return cuda_fail(e, "synchronise before free");
+        }
+    }
+    free_plan(p);
+    return LRB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,57 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "../../include/lrbatch.h"
+
+namespace lrb {
+
+// Device copy of one entry; the same field layout as lrb_gemm_desc.
+struct DevDesc {
+    const double* A;
+    const double* B;
+    double* C;
+    int32_t m, n, k;
+    int32_t lda, ldb, ldc;
+};
+static_assert(sizeof(DevDesc) == sizeof(lrb_gemm_desc), "descriptor layout");
+
+// One output tile of one entry: rows [row0, row0+BM), cols [col0, col0+BN)
+// of the variant's tile extent (clipped to the entry at run time).
+struct Item {
+    int32_t entry;
+    int32_t row0;
+    int32_t col0;
+    int32_t variant;
+};
+
+// FP64 tile variants.  128 threads = 4 warps per CTA.
+//  DFMA variants: lanes run along rows (row = lane + 32 i, i < TM), warps
+//  along columns (WN groups of TN columns) and along k (SK groups that split
+//  each k-step and are summed at the end).  BM = 32 TM, BN = WN TN.
+//  DMMA variants: FP64 tensor-core m8n8k4 fragments; each warp owns 16 rows
+//  of a 64 x BN tile.
+struct Variant {
+    int tm, tn, wn, sk, dmma;
+    int bm() const { return dmma ? 64 : 32 * tm; }
+    int bn() const { return dmma ? 8 * tn : wn * tn; }
+};
+
+constexpr int kThreads = 128;
+constexpr int kBK = 16;          // k-step staged in shared memory
+constexpr int kNumVariants = 10;
+
+// Host-side copy of the variant table (same order as the device dispatch).
+extern const Variant kVariants[kNumVariants];
+
+size_t variant_smem_bytes(int v);
+size_t max_smem_bytes();
+
+// Kernel launchers (fp64_tiles.cu).
+cudaError_t launch_persistent(const DevDesc* d_descs, const Item* d_items, int n_items,
+                              int* d_head, int grid, cudaStream_t s);
+cudaError_t launch_plain_group(int variant, const DevDesc* d_descs, const int32_t* d_entries,
+                               int n_entries, int tiles_m, int tiles_n, cudaStream_t s);
+int persistent_blocks_per_sm();
+
+}  // namespace lrb

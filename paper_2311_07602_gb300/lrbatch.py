@@ -1,0 +1,220 @@
+"""Thin ctypes binding of liblrbatch.so (include/lrbatch.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Functions keep the C names (lrb_create, lrb_plan_create, ...);
+Handle and Plan wrap them for convenience.  Device memory and streams come
+from PyTorch (tensor.data_ptr(), stream.cuda_stream).  Loading fails loudly
+if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblrbatch.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "lrbatch.h")
+
+LRB_OK, LRB_ERR_INVALID, LRB_ERR_ALIAS, LRB_ERR_NOMEM, LRB_ERR_BUDGET, LRB_ERR_QUEUE_FULL, \
+    LRB_ERR_TIMEOUT, LRB_ERR_DEVICE, LRB_ERR_UNSUPPORTED = range(9)
+STATUS_NAMES = {0: "LRB_OK", 1: "LRB_ERR_INVALID", 2: "LRB_ERR_ALIAS", 3: "LRB_ERR_NOMEM", 4: "LRB_ERR_BUDGET",
+                5: "LRB_ERR_QUEUE_FULL", 6: "LRB_ERR_TIMEOUT", 7: "LRB_ERR_DEVICE", 8: "LRB_ERR_UNSUPPORTED"}
+
+LRB_PREC_FP64, LRB_PREC_FP64_DMMA_ALLOWED, LRB_PREC_SPLIT_BF16_S3, LRB_PREC_SPLIT_BF16_S4, \
+    LRB_PREC_SPLIT_FP16_S3, LRB_PREC_SPLIT_FP16_S4 = range(6)
+SPLIT_PRECISIONS = {"bf16_s3": LRB_PREC_SPLIT_BF16_S3, "bf16_s4": LRB_PREC_SPLIT_BF16_S4,
+                    "fp16_s3": LRB_PREC_SPLIT_FP16_S3, "fp16_s4": LRB_PREC_SPLIT_FP16_S4}
+
+# lrb_gemm_desc: three pointers then six int32 (48 bytes, no padding)
+DESC_DTYPE = np.dtype([("A", np.uint64), ("B", np.uint64), ("C", np.uint64), ("m", np.int32), ("n", np.int32),
+                       ("k", np.int32), ("lda", np.int32), ("ldb", np.int32), ("ldc", np.int32)])
+assert DESC_DTYPE.itemsize == 48
+
+
+class lrb_plan_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("tune", ctypes.c_int32),
+                ("force_variant", ctypes.c_int32), ("check_alias", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
+
+
+class lrb_plan_info(ctypes.Structure):
+    _fields_ = [("entries", ctypes.c_int64), ("items", ctypes.c_int64), ("groups", ctypes.c_int64),
+                ("flops", ctypes.c_double), ("alg_bytes", ctypes.c_double), ("grid", ctypes.c_int32),
+                ("precision", ctypes.c_int32)]
+
+
+class LrbError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, sz, i32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32
+        sigs = {
+            "lrb_create": ([ctypes.POINTER(vp), ctypes.c_int], i32),
+            "lrb_destroy": ([vp], i32),
+            "lrb_plan_create": ([vp, vp, sz, ctypes.POINTER(lrb_plan_opts), ctypes.POINTER(vp)], i32),
+            "lrb_launch": ([vp, vp], i32),
+            "lrb_launch_plain": ([vp, vp], i32),
+            "lrb_plan_get_info": ([vp, ctypes.POINTER(lrb_plan_info)], i32),
+            "lrb_plan_destroy": ([vp], i32),
+            "lrb_validate": ([vp, sz, ctypes.POINTER(lrb_plan_opts)], i32),
+            "lrb_execute_host": ([vp, vp, sz, ctypes.POINTER(lrb_plan_opts), vp], i32),
+            "lrb_plan_tiles_host": ([vp, sz, i32, vp, sz, ctypes.POINTER(sz)], i32),
+            "lrb_variant_count": ([], i32),
+            "lrb_variant_shape": ([i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
+            "lrb_last_error": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sigs.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def declared_functions():
+    """Names of the functions include/lrbatch.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lrb_\w+)\s*\(", text)))
+
+
+def last_error() -> str:
+    return lib().lrb_last_error().decode()
+
+
+def check(status):
+    if status != LRB_OK:
+        raise LrbError(status, last_error())
+
+
+def make_opts(precision=LRB_PREC_FP64, use_graph=False, tune=True, force_variant=-1, check_alias=True):
+    o = lrb_plan_opts()
+    o.precision = precision
+    o.use_graph = int(bool(use_graph))
+    o.tune = int(bool(tune))
+    o.force_variant = force_variant
+    o.check_alias = int(bool(check_alias))
+    return o
+
+
+def descs_for(batch) -> np.ndarray:
+    """Descriptor array for a workloads.Batch whose buffers are tensors."""
+    d = np.zeros(len(batch), dtype=DESC_DTYPE)
+    d["A"] = np.uint64(batch.A.data_ptr()) + 8 * batch.offA.astype(np.uint64)
+    d["B"] = np.uint64(batch.B.data_ptr()) + 8 * batch.offB.astype(np.uint64)
+    d["C"] = np.uint64(batch.C.data_ptr()) + 8 * batch.offC.astype(np.uint64)
+    for key in ("m", "n", "k", "lda", "ldb", "ldc"):
+        d[key] = getattr(batch, key)
+    return d
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def lrb_validate(descs: np.ndarray, opts=None) -> int:
+    descs = np.ascontiguousarray(descs, dtype=DESC_DTYPE)
+    return lib().lrb_validate(descs.ctypes.data if len(descs) else None, len(descs),
+                              ctypes.byref(opts) if opts is not None else None)
+
+
+def lrb_plan_tiles_host(descs: np.ndarray, variant: int) -> np.ndarray:
+    descs = np.ascontiguousarray(descs, dtype=DESC_DTYPE)
+    n = ctypes.c_size_t(0)
+    check(lib().lrb_plan_tiles_host(descs.ctypes.data, len(descs), variant, None, 0, ctypes.byref(n)))
+    out = np.zeros((n.value, 5), dtype=np.int32)
+    check(lib().lrb_plan_tiles_host(descs.ctypes.data, len(descs), variant, out.ctypes.data, n.value,
+                                    ctypes.byref(n)))
+    return out
+
+
+def lrb_variant_count() -> int:
+    return lib().lrb_variant_count()
+
+
+def lrb_variant_shape(v: int):
+    bm, bn, dm = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    check(lib().lrb_variant_shape(v, ctypes.byref(bm), ctypes.byref(bn), ctypes.byref(dm)))
+    return bm.value, bn.value, bool(dm.value)
+
+
+class Handle:
+    """lrb_create / lrb_destroy."""
+
+    def __init__(self, device: int = 0):
+        self.ptr = ctypes.c_void_p()
+        check(lib().lrb_create(ctypes.byref(self.ptr), device))
+
+    def close(self):
+        if self.ptr:
+            check(lib().lrb_destroy(self.ptr))
+            self.ptr = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def plan(self, descs, **kw) -> "Plan":
+        return Plan(self, descs, **kw)
+
+    def execute_host(self, host_descs: np.ndarray, stream=None, **opts):
+        """lrb_execute_host: descriptors with HOST pointers; returns when host C holds the result."""
+        d = np.ascontiguousarray(host_descs, dtype=DESC_DTYPE)
+        o = make_opts(**opts)
+        check(lib().lrb_execute_host(self.ptr, d.ctypes.data, len(d), ctypes.byref(o), _stream_ptr(stream)))
+
+
+class Plan:
+    """lrb_plan_create / lrb_launch / lrb_launch_plain / lrb_plan_destroy."""
+
+    def __init__(self, handle: Handle, descs: np.ndarray, **opts):
+        self.handle = handle
+        self.descs = np.ascontiguousarray(descs, dtype=DESC_DTYPE)
+        self.opts = make_opts(**opts)
+        self.ptr = ctypes.c_void_p()
+        check(lib().lrb_plan_create(handle.ptr, self.descs.ctypes.data, len(self.descs), ctypes.byref(self.opts),
+                                    ctypes.byref(self.ptr)))
+
+    def launch(self, stream=None):
+        check(lib().lrb_launch(self.ptr, _stream_ptr(stream)))
+
+    def launch_plain(self, stream=None):
+        check(lib().lrb_launch_plain(self.ptr, _stream_ptr(stream)))
+
+    def info(self) -> dict:
+        i = lrb_plan_info()
+        check(lib().lrb_plan_get_info(self.ptr, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in lrb_plan_info._fields_}
+
+    def close(self):
+        if self.ptr:
+            check(lib().lrb_plan_destroy(self.ptr))
+            self.ptr = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,206 @@
+"""GPU parity of the FP64 path against the oracle, through the C ABI.
+
+Tolerance: relative Frobenius error <= 1e-13 per entry, and every element
+within 2 gamma_{k+1} (|C0| + |A||B|) of the oracle (both results are within
+gamma_{k+1} of the exact value for any summation order).  Integer-valued,
+identity and permutation inputs are exact in any order, so there the check
+is bitwise.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2311_07602_gb300 import lrbatch as L
+from paper_2311_07602_gb300 import workloads as W
+from tests.parity import (c0_at, check_entries, draw_samples, entry_view, host, oracle_batch,
+                          sample_check)
+
+pytestmark = pytest.mark.gpu
+
+NAN_CANARY = np.frombuffer(np.uint64(0x7FF8DEADBEEF0001).tobytes(), dtype=np.float64)[0]
+
+
+@pytest.fixture(scope="module")
+def handle():
+    h = L.Handle(0)
+    yield h
+    h.close()
+
+
+def ragged_batch(shapes, pad, seed, dist="normal", guard=64):
+    """Entries with ld = rows + pad, separated by `guard` canary elements;
+    the ld padding rows are canaries too."""
+    rng = np.random.default_rng(seed)
+    offs = {"A": [], "B": [], "C": []}
+    tot = {"A": guard, "B": guard, "C": guard}
+    m_, n_, k_, la, lb, lc = [], [], [], [], [], []
+    for (m, n, k) in shapes:
+        lda, ldb, ldc = m + pad, k + pad, m + pad
+        for key, size in (("A", lda * k), ("B", ldb * n), ("C", ldc * n)):
+            offs[key].append(tot[key])
+            tot[key] += size + guard
+        m_.append(m), n_.append(n), k_.append(k), la.append(lda), lb.append(ldb), lc.append(ldc)
+    bufs = {}
+    for key in "ABC":
+        x = np.full(tot[key], NAN_CANARY)
+        bufs[key] = x
+    for e, (m, n, k) in enumerate(shapes):
+        for key, rows, cols, ld in (("A", m, k, la[e]), ("B", k, n, lb[e]), ("C", m, n, lc[e])):
+            v = entry_view(bufs[key], offs[key][e], rows, cols, ld)
+            if dist == "int":
+                v[...] = rng.integers(-8, 9, (rows, cols))
+            else:
+                v[...] = rng.standard_normal((rows, cols))
+    arr = lambda x: np.asarray(x, dtype=np.int32)
+    return W.Batch(torch.from_numpy(bufs["A"]), torch.from_numpy(bufs["B"]), torch.from_numpy(bufs["C"]),
+                   arr(m_), arr(n_), arr(k_), arr(la), arr(lb), arr(lc),
+                   np.asarray(offs["A"], dtype=np.int64), np.asarray(offs["B"], dtype=np.int64),
+                   np.asarray(offs["C"], dtype=np.int64))
+
+
+RAGGED = [(1, 1, 1), (37, 5, 19), (100, 70, 33), (64, 8, 16), (129, 65, 130), (33, 129, 3), (200, 16, 200),
+          (65, 64, 17), (31, 31, 64), (256, 16, 256)]
+
+
+def run_gpu(handle, batch_host, launch="persistent", **opts):
+    dev = batch_host.to("cuda")
+    plan = handle.plan(L.descs_for(dev), **opts)
+    if launch == "plain":
+        plan.launch_plain()
+    else:
+        plan.launch()
+    torch.cuda.synchronize()
+    plan.close()
+    return host(dev.C)
+
+
+@pytest.mark.parametrize("variant", range(10))
+def test_every_variant_ragged_with_canaries(handle, variant):
+    b = ragged_batch(RAGGED, pad=3, seed=100 + variant)
+    Ah, Bh, C0 = host(b.A), host(b.B), host(b.C)
+    got = run_gpu(handle, b, force_variant=variant)
+    exp = oracle_batch(Ah, Bh, C0, b)
+    # canaries (guards between entries and ld padding) are untouched, bitwise
+    written = np.zeros(len(C0), dtype=bool)
+    for e in range(len(b)):
+        entry_view(written, int(b.offC[e]), int(b.m[e]), int(b.n[e]), int(b.ldc[e]))[...] = True
+    assert np.array_equal(got[~written].view(np.uint64), C0[~written].view(np.uint64))
+    check_entries(got, exp, Ah, Bh, C0, b)
+
+
+@pytest.mark.parametrize("variant", range(10))
+def test_integer_inputs_bitwise(handle, variant):
+    b = ragged_batch(RAGGED, pad=1, seed=200 + variant, dist="int")
+    Ah, Bh, C0 = host(b.A), host(b.B), host(b.C)
+    got = run_gpu(handle, b, force_variant=variant)
+    exp = oracle_batch(Ah, Bh, C0, b)
+    assert np.array_equal(got.view(np.uint64), exp.view(np.uint64))
+
+
+def test_identity_and_permutation_bitwise(handle):
+    rng = np.random.default_rng(3)
+    for b_, r in [(64, 16), (100, 8), (257, 33)]:
+        for kind in ("eye", "perm"):
+            P = np.eye(b_) if kind == "eye" else np.eye(b_)[rng.permutation(b_)]
+            Bm = rng.standard_normal((b_, r))
+            Cm = rng.standard_normal((b_, r))
+            A = torch.tensor(P.ravel(order="F"), device="cuda")
+            B = torch.tensor(Bm.ravel(order="F"), device="cuda")
+            C = torch.tensor(Cm.ravel(order="F"), device="cuda")
+            d = np.zeros(1, dtype=L.DESC_DTYPE)
+            d[0] = (A.data_ptr(), B.data_ptr(), C.data_ptr(), b_, r, b_, b_, b_, b_)
+            with handle.plan(d) as p:
+                p.launch()
+                torch.cuda.synchronize()
+            got = C.cpu().numpy().reshape(r, b_).T
+            assert np.array_equal(got, Cm + P @ Bm)
+
+
+def test_small_o_form_full_parity(handle):
+    """O-form, 64 x C(256x256) += A(256x16) B(16x256), U[-1,1], seed 0."""
+    b = W.small_o_form()
+    Ah, Bh, C0 = host(b.A), host(b.B), host(b.C)
+    exp = oracle_batch(Ah, Bh, C0, b)
+    dev = b.to("cuda")
+    with handle.plan(L.descs_for(dev), use_graph=True) as p:
+        p.launch()
+        torch.cuda.synchronize()
+    got = host(dev.C)
+    check_entries(got, exp, Ah, Bh, C0, b)
+    dev2 = b.to("cuda")
+    with handle.plan(L.descs_for(dev2)) as p:
+        p.launch_plain()
+        torch.cuda.synchronize()
+    assert np.array_equal(host(dev2.C).view(np.uint64), got.view(np.uint64))
+
+
+def test_persistent_plain_graph_bitwise_and_repeatable(handle):
+    forms, bs, rs = W.variable_shapes(300, seed=31, bmin=16, bmax=600)
+    base = W.variable_batch(forms, bs, rs, seed=31)
+    Ah, Bh, C0 = host(base.A), host(base.B), host(base.C)
+    outs = {}
+    for mode in ("persistent", "graph", "plain", "persistent2"):
+        dev = base.to("cuda")
+        with handle.plan(L.descs_for(dev), use_graph=(mode == "graph")) as p:
+            if mode == "plain":
+                p.launch_plain()
+            else:
+                p.launch()
+            torch.cuda.synchronize()
+        outs[mode] = host(dev.C)
+    for mode in ("graph", "plain", "persistent2"):
+        assert np.array_equal(outs[mode].view(np.uint64), outs["persistent"].view(np.uint64)), mode
+    exp = oracle_batch(Ah, Bh, C0, base)
+    check_entries(outs["persistent"], exp, Ah, Bh, C0, base)
+
+
+def test_relaunch_accumulates(handle):
+    b = ragged_batch([(70, 20, 40)], pad=0, seed=9, dist="int")
+    Ah, Bh, C0 = host(b.A), host(b.B), host(b.C)
+    dev = b.to("cuda")
+    with handle.plan(L.descs_for(dev), use_graph=True) as p:
+        p.launch()
+        p.launch()
+        torch.cuda.synchronize()
+    once = oracle_batch(Ah, Bh, C0, b)
+    twice = oracle_batch(Ah, Bh, once, b)
+    assert np.array_equal(host(dev.C).view(np.uint64), twice.view(np.uint64))
+
+
+def test_uniform_sweep_full_size_sampled(handle):
+    """All 18 uniform groups (b in {256,512,1024} x r in {16,32,64} x T/O,
+    batch 4096/1024/256) in ONE persistent graph launch, as the benchmark
+    times them; sampled outputs against the oracle."""
+    batches = [W.uniform_batch(f, b_, r, n, dist="normal", seed=s, device="cuda")
+               for f, b_, r, n, s in W.uniform_sweep_groups()]
+    descs = np.concatenate([L.descs_for(b) for b in batches])
+    samples = [draw_samples(b, 150, seed=i, extra_entries=[0, len(b) - 1]) for i, b in enumerate(batches)]
+    c0s = [c0_at(b, s) for b, s in zip(batches, samples)]
+    with handle.plan(descs, use_graph=True) as p:
+        p.launch()
+        torch.cuda.synchronize()
+    for b, s, c0 in zip(batches, samples, c0s):
+        sample_check(b, b.C, c0, s)
+
+
+def test_variable_size_full_size_sampled(handle):
+    """20,000 entries, b log-uniform in [64, 2048], r in {8,...,128}, T/O
+    50/50, operands from a shared 4 GB pool, one graph-captured persistent
+    launch with autotuned tiles; sampled outputs (incl. the 50 largest and
+    smallest entries) against the oracle."""
+    forms, bs, rs = W.variable_shapes(20000, seed=3)
+    b = W.variable_batch(forms, bs, rs, seed=3, device="cuda", pool_elems=(4 << 30) // 8)
+    flops = 2.0 * b.m * b.n * b.k
+    order = np.argsort(flops)
+    extra = np.concatenate([order[:50], order[-50:]])
+    s = draw_samples(b, 3000, seed=5, extra_entries=extra)
+    c0 = c0_at(b, s)
+    with handle.plan(L.descs_for(b), use_graph=True) as p:
+        p.launch()
+        torch.cuda.synchronize()
+    sample_check(b, b.C, c0, s)
+    del b
+    torch.cuda.empty_cache()

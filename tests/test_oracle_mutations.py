@@ -1,0 +1,152 @@
+"""The pins are strong enough: each plausible mistake, planted in a
+temporary copy of the oracle (on the CPU), makes at least one pin fail.
+
+C oracle: a flipped sign, a dropped last term, a transposed B index, the
+wrong leading dimension for A or C.  Split oracle: floor instead of
+round-to-nearest, an off-by-one exponent, a dropped digit level, digits
+combined with the wrong weight."""
+import ctypes
+import importlib.util
+import os
+import subprocess
+import sys
+import types
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import PRESETS
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ORACLE_DIR = os.path.join(os.path.dirname(HERE), "oracle")
+
+C_MUTATIONS = {
+    "sign": ("c[i] = c[i] + prod;", "c[i] = c[i] - prod;"),
+    "dropped_term": ("for (int32_t p = 0; p < k; ++p) {\n            const double* a",
+                     "for (int32_t p = 0; p < k - 1; ++p) {\n            const double* a"),
+    "transposed_B": ("double b = B[(size_t)p + (size_t)j * (size_t)ldb];",
+                     "double b = B[(size_t)j + (size_t)p * (size_t)ldb];"),
+    "wrong_lda": ("const double* a = A + (size_t)p * (size_t)lda;", "const double* a = A + (size_t)p * (size_t)m;"),
+    "wrong_ldc": ("double* c = C + (size_t)j * (size_t)ldc;", "double* c = C + (size_t)j * (size_t)m;"),
+}
+
+
+def build_mutant(tmp_path, old, new):
+    src = open(os.path.join(ORACLE_DIR, "oracle_gemm.c")).read()
+    assert src.count(old) == 1, old
+    path = tmp_path / "mut.c"
+    path.write_text(src.replace(old, new))
+    so = tmp_path / "libmut.so"
+    subprocess.run(["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC",
+                    "-o", str(so), str(path), "-lm"], check=True)
+    L = ctypes.CDLL(str(so))
+    dp = ctypes.POINTER(ctypes.c_double)
+    i32 = ctypes.c_int32
+    L.oracle_gemm.argtypes = [i32, i32, i32, dp, i32, dp, i32, dp, i32]
+    return L
+
+
+def pins_pass_c(L) -> bool:
+    """A compact run of the FP64 pins against library L."""
+    dp = ctypes.POINTER(ctypes.c_double)
+    rng = np.random.default_rng(0)
+
+    def run(m, n, k, A, lda, B, ldb, C, ldc):
+        a = np.ascontiguousarray(A.ravel(order="F"))
+        b = np.ascontiguousarray(B.ravel(order="F"))
+        c = np.ascontiguousarray(C.ravel(order="F")).copy()
+        L.oracle_gemm(m, n, k, a.ctypes.data_as(dp), lda, b.ctypes.data_as(dp), ldb, c.ctypes.data_as(dp), ldc)
+        return c.reshape(C.shape, order="F")
+
+    for m, n, k in [(5, 4, 3), (17, 5, 33)]:
+        pad = 2
+        A = np.zeros((m + pad, k))
+        A[:m] = rng.integers(-8, 9, (m, k))
+        B = np.zeros((k + pad, n))
+        B[:k] = rng.integers(-8, 9, (k, n))
+        C = np.zeros((m + pad, n))
+        C[:m] = rng.integers(-100, 100, (m, n))
+        out = run(m, n, k, A, m + pad, B, k + pad, C, m + pad)
+        exact = C[:m] + A[:m] @ B[:k]
+        if not np.array_equal(out[:m], exact) or not np.array_equal(out[m:], C[m:]):
+            return False
+    return True
+
+
+def test_unmutated_oracle_passes():
+    assert pins_pass_c(oracle.lib())
+
+
+@pytest.mark.parametrize("name", sorted(C_MUTATIONS))
+def test_c_mutation_is_caught(tmp_path, name):
+    old, new = C_MUTATIONS[name]
+    assert not pins_pass_c(build_mutant(tmp_path, old, new))
+
+
+SPLIT_MUTATIONS = {
+    "floor_not_rint": ("Z = np.rint(np.ldexp(", "Z = np.floor(np.ldexp("),
+    "exponent_off_by_one": ("return np.where(mu == 0, 0, e).astype(np.int64)",
+                            "return np.where(mu == 0, 0, e - 1).astype(np.int64)"),
+    "dropped_level": ("        for L in sorted(levels):\n            scale",
+                      "        for L in sorted(levels)[:-1]:\n            scale"),
+    "wrong_weight": ("scale = (E[:, None] + F[None, :] - p.beta * L)", "scale = (E[:, None] + F[None, :] - p.beta * (L - 1))"),
+}
+
+
+def load_split_mutant(old, new) -> types.ModuleType:
+    src = open(os.path.join(ORACLE_DIR, "split.py")).read()
+    assert src.count(old) == 1, old
+    mod = types.ModuleType("split_mutant")
+    sys.modules["split_mutant"] = mod          # dataclasses look the module up
+    try:
+        exec(compile(src.replace(old, new), "split_mutant", "exec"), mod.__dict__)
+    finally:
+        del sys.modules["split_mutant"]
+    return mod
+
+
+def split_pins_pass(S) -> bool:
+    p = PRESETS["bf16_s3"]
+    rng = np.random.default_rng(1)
+    # integer inputs: exact product
+    m, n, k = 6, 5, p.kc + 9
+    A = rng.integers(-8, 9, (m, k)).astype(np.float64)
+    B = rng.integers(-8, 9, (k, n)).astype(np.float64)
+    C = rng.integers(-50, 50, (m, n)).astype(np.float64)
+    if not np.array_equal(S.split_gemm(A, B, C, p), C + A @ B):
+        return False
+    # digits reconstruct the correctly rounded value
+    x = rng.standard_normal((3, 20)) * 10.0 ** rng.uniform(-3, 3, (3, 20))
+    E = S.chunk_exponents(x, axis=1)
+    for i in range(3):
+        mu = max(abs(Fraction(v)) for v in x[i])
+        if not (Fraction(2) ** (int(E[i]) - 1) <= mu < Fraction(2) ** int(E[i])):
+            return False
+    D = S.split_digits(x, E[:, None], p)
+    rec = S.reconstruct(D, E[:, None], p)
+    if np.any(np.abs(rec - x) > np.ldexp(1.0, (E[:, None] - p.beta * p.S - 1).astype(np.int32))):
+        return False
+    # a-priori bound on random data
+    A = rng.standard_normal((4, 40))
+    B = rng.standard_normal((40, 3))
+    C = np.zeros((4, 3))
+    out = S.split_gemm(A, B, C, p)
+    bnd = oracle.apriori_bound(A, B, C, p)
+    for i in range(4):
+        for j in range(3):
+            exact = sum(Fraction(A[i, q]) * Fraction(B[q, j]) for q in range(40))
+            if abs(Fraction(out[i, j]) - exact) > Fraction(bnd[i, j]):
+                return False
+    return True
+
+
+def test_unmutated_split_oracle_passes():
+    import oracle.split as S
+    assert split_pins_pass(S)
+
+
+@pytest.mark.parametrize("name", sorted(SPLIT_MUTATIONS))
+def test_split_mutation_is_caught(name):
+    assert not split_pins_pass(load_split_mutant(*SPLIT_MUTATIONS[name]))
