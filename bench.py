@@ -164,7 +164,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lrbatch", choices=["lrbatch", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--cpu-fraction", type=float, default=0.25)
+    ap.add_argument("--cpu-fraction", type=float, default=1.0)
     ap.add_argument("--ref-fraction", type=float, default=1 / 32)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -274,8 +274,8 @@ def main():
     if not args.no_cpu and rank == 0 and world == 1:
         f, s, used, ents = cpu_baseline(args.cpu_fraction)
         line["cpu_baseline"] = {"value": round(f / s / 1e9, 3), "unit": UNIT, "cores": used, "kind": "oracle",
-                                "sample": f"first {args.cpu_fraction:.3g} of every group of the sweep "
-                                          f"({ents} entries, {f:.3g} flops, {s:.1f} s)"}
+                                "sample": (f"first {args.cpu_fraction:.3g} of every group of the sweep "
+                                           f"({ents} entries, {f:.3g} flops, {s:.1f} s on the host cores)")}
     plan.close()
     handle.close()
     if rank == 0:
