@@ -162,6 +162,26 @@ lrb_status lrb_plan_tiles_host(const lrb_gemm_desc* host_descs, size_t count, in
 int32_t lrb_variant_count(void);
 lrb_status lrb_variant_shape(int32_t variant, int32_t* bm, int32_t* bn, int32_t* is_dmma);
 
+/* ---- launch without device allocation -----------------------------------
+ * The paper has no counterpart: this serves callers that cannot call
+ * cudaMalloc (their GPU memory is owned by a framework pool or a fixed
+ * budget, or their loop must not risk the device-wide synchronisation of
+ * cudaMalloc/cudaFree).  Runs C += A B for `count` entries (device operand
+ * pointers, host descriptor array, same rules as lrb_plan_create) as one
+ * persistent FP64 launch on `stream`, with untuned tiles, using only a
+ * fixed file-scope device array for the descriptors, tiles and work counter
+ * -- nothing is allocated.  Limits: count <= LRB_NOALLOC_MAX_ENTRIES and at
+ * most LRB_NOALLOC_MAX_TILES output tiles (64 x 8..64 each); larger batches
+ * return LRB_ERR_INVALID before any CUDA call.  The array (about 4.2 MB) is
+ * held on every GPU that loads the library until the process exits.  All
+ * calls share it, so calls that overlap on the GPU race: order them on one
+ * stream.  The first call on a device looks up the array's address and the
+ * kernel's limits; make it before any stream capture.  Asynchronous like
+ * lrb_launch (the descriptor array is copied before the call returns). */
+#define LRB_NOALLOC_MAX_ENTRIES 4096
+#define LRB_NOALLOC_MAX_TILES 262144
+lrb_status lrb_launch_noalloc(const lrb_gemm_desc* host_descs, size_t count, void* stream);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char* lrb_last_error(void);
 

@@ -407,6 +407,8 @@ void free_plan(lrb_plan* p) {
 
 }  // namespace
 
+void lrb::set_last_error(const char* msg) { g_err = msg; }
+
 extern "C" {
 
 const char* lrb_last_error(void) { return g_err.c_str(); }

@@ -54,4 +54,7 @@ cudaError_t launch_plain_group(int variant, const DevDesc* d_descs, const int32_
                                int n_entries, int tiles_m, int tiles_n, cudaStream_t s);
 int persistent_blocks_per_sm();
 
+// Sets the calling thread's lrb_last_error() message (api.cu).
+void set_last_error(const char* msg);
+
 }  // namespace lrb

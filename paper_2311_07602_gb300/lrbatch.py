@@ -73,6 +73,7 @@ def lib():
             "lrb_plan_destroy": ([vp], i32),
             "lrb_validate": ([vp, sz, ctypes.POINTER(lrb_plan_opts)], i32),
             "lrb_execute_host": ([vp, vp, sz, ctypes.POINTER(lrb_plan_opts), vp], i32),
+            "lrb_launch_noalloc": ([vp, sz, vp], i32),
             "lrb_plan_tiles_host": ([vp, sz, i32, vp, sz, ctypes.POINTER(sz)], i32),
             "lrb_variant_count": ([], i32),
             "lrb_variant_shape": ([i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
@@ -146,6 +147,21 @@ def lrb_plan_tiles_host(descs: np.ndarray, variant: int) -> np.ndarray:
     check(lib().lrb_plan_tiles_host(descs.ctypes.data, len(descs), variant, out.ctypes.data, n.value,
                                     ctypes.byref(n)))
     return out
+
+
+NOALLOC_MAX_ENTRIES = 4096      # LRB_NOALLOC_MAX_ENTRIES
+NOALLOC_MAX_TILES = 262144      # LRB_NOALLOC_MAX_TILES
+
+
+def lrb_launch_noalloc(descs: np.ndarray, stream=None) -> int:
+    """lrb_launch_noalloc: the batch as one persistent FP64 launch that
+    allocates no device memory (its scratch is a fixed array inside the
+    library).  For callers that cannot call cudaMalloc -- e.g. their GPU
+    memory belongs to a framework pool or a fixed budget, or their loop must
+    not risk the device-wide synchronisation an allocation can cause.
+    Returns the status code."""
+    d = np.ascontiguousarray(descs, dtype=DESC_DTYPE)
+    return lib().lrb_launch_noalloc(d.ctypes.data if len(d) else None, len(d), _stream_ptr(stream))
 
 
 def lrb_variant_count() -> int:
