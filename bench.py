@@ -41,6 +41,11 @@ UNIT = "GFLOP/s"
 WORKLOAD = ("uniform-shape FP64 sweep: b in {256,512,1024} (batch 4096/1024/256) x r in {16,32,64} x "
             "T-form (b x b)(b x r) and O-form (b x r)(r x b), N(0,1), one persistent graph launch per step")
 DFMA_LANES_PER_SM_CLK = 2          # FP64 FMA lanes per SM per clock on GB300 (1.25 TFLOP/s nominal)
+# DRAM bytes per algorithmic byte of k_persistent, from the ncu capture in
+# profiles/k_persistent_fp64_uniform_sweep.md (small case of the same sweep),
+# valid while fp64_tiles.cu has the SHA-256 prefix below.
+TRAFFIC_PER_ALG_BYTE = 1.959e9 / 2.018344960e9
+TRAFFIC_SOURCE_SHA = "90b6a78a72fcf2dc"
 
 
 def dist_env():
@@ -101,9 +106,15 @@ def fp64_peak_tflops(props, sm_max_mhz) -> float:
     return props.multi_processor_count * DFMA_LANES_PER_SM_CLK * 2 * sm_max_mhz * 1e6 / 1e12
 
 
-def sweep_batches(device):
+def kernel_sha() -> str:
+    import hashlib
+    path = os.path.join(ROOT, "paper_2311_07602_gb300", "csrc", "fp64_tiles.cu")
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def sweep_batches(device, scale=1.0):
     from paper_2311_07602_gb300 import workloads as W
-    return [W.uniform_batch(f, b, r, n, dist="normal", seed=s, device=device)
+    return [W.uniform_batch(f, b, r, max(1, int(round(n * scale))), dist="normal", seed=s, device=device)
             for f, b, r, n, s in W.uniform_sweep_groups()]
 
 
@@ -169,6 +180,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="batch-count scale of every group (profiling runs use a small case)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -197,7 +210,7 @@ def main():
         return float(t.item())
 
     from paper_2311_07602_gb300 import lrbatch as L
-    batches = sweep_batches(dev)
+    batches = sweep_batches(dev, args.scale)
     descs = np.concatenate([L.descs_for(b) for b in batches])
     flops = float(sum(b.flops() for b in batches))
     alg_bytes = float(sum(b.alg_bytes() for b in batches))
@@ -247,13 +260,19 @@ def main():
             "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded N(0,1), generated on the device)",
-            "config": {"workload": WORKLOAD, "entries": int(info["entries"]), "tiles": int(info["items"]),
+            "config": {"workload": WORKLOAD if args.scale == 1.0 else f"{WORKLOAD} (batch counts x {args.scale})",
+                       "entries": int(info["entries"]), "tiles": int(info["items"]),
                        "flops_per_step": flops, "alg_bytes_per_step": alg_bytes, "persistent_grid": int(info["grid"]),
                        "l2": "inputs larger than L2 (%.0f GB per step), no flush" % (alg_bytes / 1e9),
                        "plan_s": round(plan_s, 3)},
             "gpu_launches": args.steps,
             "roofline": {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
-                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "frac": round(achieved / peak, 4),
+                         "traffic": (round(TRAFFIC_PER_ALG_BYTE * alg_bytes) if kernel_sha() == TRAFFIC_SOURCE_SHA
+                                     else None),
+                         "traffic_note": "DRAM bytes per launch, scaled by algorithmic bytes from the small-case ncu "
+                                         "capture (profiles/k_persistent_fp64_uniform_sweep.md); null if the kernel "
+                                         "source changed since",
                          "kernel": "k_persistent (FP64 DFMA tiles)",
                          "peak_source": "derived: SMs x 2 DFMA lanes/clk x 2 flop x max SM clock",
                          "peak_measured_probe_tflops": 1.2029},

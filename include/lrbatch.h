@@ -128,6 +128,21 @@ lrb_status lrb_launch_plain(lrb_plan* p, void* stream);
 
 lrb_status lrb_plan_get_info(const lrb_plan* p, lrb_plan_info* info);
 
+/* Synchronises the plan's last stream and reports whether any of its
+ * launches hit a bounded device-side wait (the split-precision kernel waits
+ * on its tensor-core completion barrier with an iteration limit; on expiry it
+ * releases its TMEM, leaves its C tile unwritten and sets a status word):
+ * LRB_ERR_TIMEOUT if so (sticky), LRB_OK otherwise. */
+lrb_status lrb_plan_status(lrb_plan* p);
+
+/* Diagnostic for split-precision plans of ONE entry: launches the plan once
+ * (C += A B as lrb_launch does) and also writes every k-chunk's FP32 level
+ * sums P_L (the tensor-core accumulators before recombination) to the
+ * device array `dump` laid out as float[chunks][S][m][n], chunks =
+ * ceil(k / kc) (kc = 128 for BF16, 32 for FP16), level L = index + 2.
+ * LRB_ERR_UNSUPPORTED for FP64 plans or plans of several entries. */
+lrb_status lrb_split_dump_levels(lrb_plan* p, float* dump, void* stream);
+
 /* Frees the plan's device memory after synchronising its last stream. */
 lrb_status lrb_plan_destroy(lrb_plan* p);
 

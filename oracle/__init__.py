@@ -21,8 +21,8 @@ import numpy as np
 
 from . import build as _build
 from .split import (PRESETS, SplitParams, apriori_bound, chunk_exponents,  # noqa: F401
-                    chunk_level_sums, level_bound, reconstruct, split_digits,
-                    split_gemm)
+                    chunk_level_sums, level_bound, recombination_magnitude,
+                    reconstruct, split_digits, split_dot_samples, split_gemm)
 
 _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)

@@ -193,3 +193,45 @@ def apriori_bound(A: np.ndarray, B: np.ndarray, C: np.ndarray, p: SplitParams) -
         nterms += len(p.levels())
     g = nterms * u / (1 - nterms * u)
     return bound * (1 + 8 * u) + g * mag * (1 + 8 * u)
+
+
+def split_dot_samples(arow: np.ndarray, bcol: np.ndarray, c0: np.ndarray, p: SplitParams) -> np.ndarray:
+    """Selected outputs of split_gemm, one per sample: arow (q, k) holds row i
+    of A, bcol (q, k) column j of B, c0 (q,) the old C value.  Row and column
+    exponents depend only on that row and column, so each output follows the
+    module definition exactly (same additions in the same order)."""
+    arow = np.asarray(arow, dtype=np.float64)
+    bcol = np.asarray(bcol, dtype=np.float64)
+    out = np.array(c0, dtype=np.float64, copy=True)
+    k = arow.shape[1]
+    nchunks = (k + p.kc - 1) // p.kc
+    for c in range(nchunks):
+        lo, hi = c * p.kc, min((c + 1) * p.kc, k)
+        Ar, Bc = arow[:, lo:hi], bcol[:, lo:hi]
+        E = chunk_exponents(Ar, axis=1)
+        F = chunk_exponents(Bc, axis=1)
+        DA = split_digits(Ar, E[:, None], p)
+        DB = split_digits(Bc, F[:, None], p)
+        levels = {}
+        for s, t in p.kept_pairs():
+            P = np.sum(DA[s - 1] * DB[t - 1], axis=1)
+            L = s + t
+            levels[L] = levels.get(L, 0) + P
+        for L in sorted(levels):
+            out = out + np.ldexp(levels[L].astype(np.float64), (E + F - p.beta * L).astype(np.int32))
+    return out
+
+
+def recombination_magnitude(A: np.ndarray, B: np.ndarray, C: np.ndarray, p: SplitParams) -> np.ndarray:
+    """|C| + sum over chunks and levels of |2^(E+F-beta L) P_L|: the size of
+    everything the binary64 recombination adds, for rounding-error bounds of
+    a recombination that adds the same exact terms in another grouping."""
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    mag = np.abs(np.asarray(C, dtype=np.float64)).copy()
+    nchunks = (A.shape[1] + p.kc - 1) // p.kc
+    for c in range(nchunks):
+        E, F, levels = chunk_level_sums(A, B, p, c)
+        for L, P in levels.items():
+            mag += np.ldexp(np.abs(P).astype(np.float64), (E[:, None] + F[None, :] - p.beta * L).astype(np.int32))
+    return mag

@@ -194,7 +194,8 @@ int heuristic_variant(int m, int n, int k, bool dmma_ok) {
 struct lrb_handle {
     int device = 0;
     int sms = 0;
-    int blocks_per_sm = 0;
+    int blocks_per_sm = 0;        // narrow persistent kernel
+    int blocks_per_sm_wide = 0;   // wide persistent kernel
     std::string gpu_key;
     std::string cache_path;
     std::map<std::string, int> tuned;
@@ -221,6 +222,7 @@ struct lrb_plan {
     int* d_head = nullptr;
     int n_items = 0;
     int grid = 0;
+    bool wide = false;   // some tile needs the wide persistent kernel
     std::vector<Group> groups;
     bool use_graph = false;
     cudaGraph_t graph = nullptr;
@@ -323,6 +325,7 @@ lrb_status tune_bucket(lrb_handle* h, int m, int n, int k, bool dmma_ok, int* be
     *best = heuristic_variant(m, n, k, dmma_ok);
     for (int v = 0; v < kNumVariants; ++v) {
         const Variant& V = kVariants[v];
+        if (!variant_is_narrow(v)) continue;   // tuned plans keep the 4-CTA persistent kernel
         if (V.dmma && !dmma_ok) continue;
         // skip tiles more than twice as tall/wide as the shape needs
         if (V.bm() > 32 && V.bm() >= 2 * std::max(M, 32)) continue;
@@ -472,8 +475,9 @@ lrb_status lrb_create(lrb_handle** out, int device) {
         return cuda_fail(e, "cudaGetDeviceProperties");
     }
     h->sms = prop.multiProcessorCount;
-    h->blocks_per_sm = persistent_blocks_per_sm();
-    if (h->blocks_per_sm <= 0) {
+    h->blocks_per_sm = persistent_blocks_per_sm(false);
+    h->blocks_per_sm_wide = persistent_blocks_per_sm(true);
+    if (h->blocks_per_sm <= 0 || h->blocks_per_sm_wide <= 0) {
         delete h;
         return fail(LRB_ERR_DEVICE, "persistent kernel does not fit on this device");
     }
@@ -607,7 +611,9 @@ lrb_status lrb_plan_create(lrb_handle* h, const lrb_gemm_desc* host_descs, size_
         free_plan(p);
         return cuda_fail(ce, "plan upload");
     }
-    p->grid = std::max(1, std::min(h->sms * h->blocks_per_sm, p->n_items));
+    for (size_t e = 0; e < count; ++e)
+        if (!variant_is_narrow(var[e])) p->wide = true;
+    p->grid = std::max(1, std::min(h->sms * (p->wide ? h->blocks_per_sm_wide : h->blocks_per_sm), p->n_items));
     p->info.items = p->n_items;
     p->info.groups = (int64_t)p->groups.size();
     p->info.grid = p->grid;
@@ -616,7 +622,7 @@ lrb_status lrb_plan_create(lrb_handle* h, const lrb_gemm_desc* host_descs, size_
         cudaStream_t cs = h->stream;
         ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (ce == cudaSuccess) {
-            cudaError_t le = launch_persistent(p->d_descs, p->d_items, p->n_items, p->d_head, p->grid, cs);
+            cudaError_t le = launch_persistent(p->d_descs, p->d_items, p->n_items, p->d_head, p->grid, cs, p->wide);
             ce = cudaStreamEndCapture(cs, &p->graph);
             if (le != cudaSuccess) ce = le;
         }
@@ -642,7 +648,7 @@ lrb_status lrb_launch(lrb_plan* p, void* stream) {
         return e == cudaSuccess ? LRB_OK : cuda_fail(e, "split launch");
     }
     cudaError_t e = p->use_graph ? cudaGraphLaunch(p->exec, s)
-                                 : launch_persistent(p->d_descs, p->d_items, p->n_items, p->d_head, p->grid, s);
+                                 : launch_persistent(p->d_descs, p->d_items, p->n_items, p->d_head, p->grid, s, p->wide);
     if (e != cudaSuccess) return cuda_fail(e, "persistent launch");
     return LRB_OK;
 }
@@ -785,6 +791,29 @@ lrb_status lrb_execute_host(lrb_handle* h, const lrb_gemm_desc* host_descs, size
     for (const Copy& c : d2h) LRB_CUDA(copy(c, false));
     LRB_CUDA(cudaStreamSynchronize(s));
     return LRB_OK;
+}
+
+lrb_status lrb_plan_status(lrb_plan* p) {
+    if (!p) return fail(LRB_ERR_INVALID, "plan is NULL");
+    LRB_CUDA(cudaSetDevice(p->h->device));
+    if (p->launched) LRB_CUDA(p->last_stream ? cudaStreamSynchronize(p->last_stream) : cudaDeviceSynchronize());
+    if (p->sp) {
+        int v = 0;
+        if (split::read_status(p->sp, p->last_stream, &v) != 0) return fail(LRB_ERR_DEVICE, "reading plan status");
+        if (v) return fail(LRB_ERR_TIMEOUT, "a bounded device wait expired in a split-precision launch");
+    }
+    return LRB_OK;
+}
+
+lrb_status lrb_split_dump_levels(lrb_plan* p, float* dump, void* stream) {
+    if (!p || !dump) return fail(LRB_ERR_INVALID, "NULL argument");
+    if (!p->sp || p->descs.size() != 1) return fail(LRB_ERR_UNSUPPORTED, "needs a split-precision plan of one entry");
+    cudaStream_t s = (cudaStream_t)stream;
+    LRB_CUDA(cudaSetDevice(p->h->device));
+    p->last_stream = s;
+    p->launched = true;
+    cudaError_t e = split::launch_dump(p->sp, dump, s);
+    return e == cudaSuccess ? LRB_OK : cuda_fail(e, "split dump launch");
 }
 
 lrb_status lrb_plan_get_info(const lrb_plan* p, lrb_plan_info* info) {

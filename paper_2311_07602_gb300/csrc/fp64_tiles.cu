@@ -16,6 +16,8 @@
 //     copies suffice and work for any leading dimension).
 // The same tile functions serve the persistent work-queue kernel and the
 // one-launch-per-shape kernels, so both give bitwise identical results.
+#include <algorithm>
+
 #include "lrb_internal.h"
 
 namespace lrb {
@@ -286,6 +288,9 @@ __device__ __forceinline__ void tile_dmma(const DevDesc& d, int m0, int n0, doub
         }
 }
 
+// WIDE = false dispatches only the variants that fit 128 registers per
+// thread, so the narrow persistent kernel keeps 4 CTAs (16 warps) per SM.
+template <bool WIDE>
 __device__ __forceinline__ void run_tile(int variant, const DevDesc& d, int m0, int n0, double* smem) {
     switch (variant) {
         case 0: tile_dfma<2, 2, 4, 1>(d, m0, n0, smem); break;
@@ -293,11 +298,11 @@ __device__ __forceinline__ void run_tile(int variant, const DevDesc& d, int m0, 
         case 2: tile_dfma<2, 8, 4, 1>(d, m0, n0, smem); break;
         case 3: tile_dfma<2, 16, 4, 1>(d, m0, n0, smem); break;
         case 4: tile_dfma<4, 8, 4, 1>(d, m0, n0, smem); break;
-        case 5: tile_dfma<4, 16, 4, 1>(d, m0, n0, smem); break;
+        case 5: if constexpr (WIDE) tile_dfma<4, 16, 4, 1>(d, m0, n0, smem); break;
         case 6: tile_dfma<1, 8, 1, 4>(d, m0, n0, smem); break;
         case 7: tile_dfma<1, 16, 2, 2>(d, m0, n0, smem); break;
         case 8: tile_dmma<4>(d, m0, n0, smem); break;
-        case 9: tile_dmma<8>(d, m0, n0, smem); break;
+        case 9: if constexpr (WIDE) tile_dmma<8>(d, m0, n0, smem); break;
         default: break;   // planner never emits other ids
     }
 }
@@ -305,20 +310,23 @@ __device__ __forceinline__ void run_tile(int variant, const DevDesc& d, int m0, 
 // Persistent kernel: each CTA takes the next tile from the work counter until
 // the list (ordered longest-first by the planner) is exhausted.  No CTA ever
 // waits for another; the counter is the only shared state.
-__global__ void __launch_bounds__(kThreads) k_persistent(const DevDesc* __restrict__ descs,
-                                                         const Item* __restrict__ items, int n_items,
-                                                         int* __restrict__ head) {
+template <bool WIDE>
+__global__ void __launch_bounds__(kThreads, WIDE ? 1 : 3) k_persistent(const DevDesc* __restrict__ descs,
+                                                                      const Item* __restrict__ items, int n_items,
+                                                                      int* __restrict__ head) {
     extern __shared__ __align__(16) double smem[];
     __shared__ int s_item;
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(head, 1);
-        __syncthreads();
-        const int it = s_item;
-        if (it >= n_items) break;
+    if (threadIdx.x == 0) s_item = atomicAdd(head, 1);
+    __syncthreads();
+    int it = s_item;
+    while (it < n_items) {
         const Item item = items[it];
         const DevDesc d = descs[item.entry];
-        run_tile(item.variant, d, item.row0, item.col0, smem);
+        __syncthreads();                                   // every thread has read s_item
+        if (threadIdx.x == 0) s_item = atomicAdd(head, 1);  // claim the next tile while this one runs
+        run_tile<WIDE>(item.variant, d, item.row0, item.col0, smem);
         __syncthreads();
+        it = s_item;
     }
 }
 
@@ -335,7 +343,7 @@ __global__ void __launch_bounds__(kThreads) k_plain(const DevDesc* __restrict__ 
     const int bm = (V == 8 || V == 9) ? 64 : (V == 4 || V == 5 ? 128 : (V >= 6 ? 32 : 64));
     const int bn = V == 0 ? 8 : V == 1 ? 16 : V == 2 ? 32 : V == 3 ? 64 : V == 4 ? 32 : V == 5 ? 64
                  : V == 6 ? 8 : V == 7 ? 32 : V == 8 ? 32 : 64;
-    run_tile(V, d, (t % tiles_m) * bm, (t / tiles_m) * bn, smem);
+    run_tile<true>(V, d, (t % tiles_m) * bm, (t / tiles_m) * bn, smem);
 }
 
 template <int V>
@@ -353,24 +361,36 @@ cudaError_t plain_launch(const DevDesc* d_descs, const int32_t* d_entries, int n
 
 }  // namespace
 
-int persistent_blocks_per_sm() {
+bool variant_is_narrow(int v) { return v != 5 && v != 9; }
+
+size_t persistent_smem_bytes(bool wide) {
+    size_t m = 0;
+    for (int v = 0; v < kNumVariants; ++v)
+        if (wide || variant_is_narrow(v)) m = std::max(m, variant_smem_bytes(v));
+    return m;
+}
+
+int persistent_blocks_per_sm(bool wide) {
     int nb = 0;
-    const size_t smem = max_smem_bytes();
-    if (cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent, kThreads, smem) != cudaSuccess) return 0;
+    const size_t smem = persistent_smem_bytes(wide);
+    auto kern = wide ? k_persistent<true> : k_persistent<false>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kThreads, smem) != cudaSuccess) return 0;
     return nb;
 }
 
 cudaError_t launch_persistent(const DevDesc* d_descs, const Item* d_items, int n_items, int* d_head, int grid,
-                              cudaStream_t s) {
+                              cudaStream_t s, bool wide) {
     // the shared-memory attribute was set by persistent_blocks_per_sm() when
     // the handle was created (not here: this may run under stream capture)
-    const size_t smem = max_smem_bytes();
+    const size_t smem = persistent_smem_bytes(wide);
     cudaError_t e = cudaMemsetAsync(d_head, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     if (n_items <= 0) return cudaSuccess;
-    k_persistent<<<grid, kThreads, smem, s>>>(d_descs, d_items, n_items, d_head);
+    if (wide)
+        k_persistent<true><<<grid, kThreads, smem, s>>>(d_descs, d_items, n_items, d_head);
+    else
+        k_persistent<false><<<grid, kThreads, smem, s>>>(d_descs, d_items, n_items, d_head);
     return cudaGetLastError();
 }
 

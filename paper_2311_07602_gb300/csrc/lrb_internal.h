@@ -48,11 +48,14 @@ size_t variant_smem_bytes(int v);
 size_t max_smem_bytes();
 
 // Kernel launchers (fp64_tiles.cu).
+// wide = false: the persistent kernel without the 128x64 DFMA and 64x64 DMMA
+// tiles (<= 128 registers, 4 CTAs per SM); wide = true: every variant.
 cudaError_t launch_persistent(const DevDesc* d_descs, const Item* d_items, int n_items,
-                              int* d_head, int grid, cudaStream_t s);
+                              int* d_head, int grid, cudaStream_t s, bool wide = false);
 cudaError_t launch_plain_group(int variant, const DevDesc* d_descs, const int32_t* d_entries,
                                int n_entries, int tiles_m, int tiles_n, cudaStream_t s);
-int persistent_blocks_per_sm();
+int persistent_blocks_per_sm(bool wide = false);
+bool variant_is_narrow(int v);
 
 // Sets the calling thread's lrb_last_error() message (api.cu).
 void set_last_error(const char* msg);

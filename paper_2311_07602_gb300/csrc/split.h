@@ -14,6 +14,13 @@ struct SplitPlan;
 lrb_status create(int device, int sms, const lrb_gemm_desc* descs, size_t count, int precision, SplitPlan** out,
                   lrb_plan_info* info);
 cudaError_t launch(SplitPlan* p, cudaStream_t s);
+// Same launch, also writing every chunk's FP32 level sums to `dump`
+// (float[chunks][S][m][n] for a single-entry plan) for the exactness test.
+cudaError_t launch_dump(SplitPlan* p, float* dump, cudaStream_t s);
+// Reads the plan's device status word (1 after a bounded wait expired).
+int read_status(SplitPlan* p, cudaStream_t s, int* value);
+int chunk_len(int precision);
+int digit_count(int precision);
 void destroy(SplitPlan* p);
 
 }  // namespace split

@@ -74,6 +74,8 @@ def lib():
             "lrb_validate": ([vp, sz, ctypes.POINTER(lrb_plan_opts)], i32),
             "lrb_execute_host": ([vp, vp, sz, ctypes.POINTER(lrb_plan_opts), vp], i32),
             "lrb_launch_noalloc": ([vp, sz, vp], i32),
+            "lrb_plan_status": ([vp], i32),
+            "lrb_split_dump_levels": ([vp, vp, vp], i32),
             "lrb_plan_tiles_host": ([vp, sz, i32, vp, sz, ctypes.POINTER(sz)], i32),
             "lrb_variant_count": ([], i32),
             "lrb_variant_shape": ([i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
@@ -218,6 +220,13 @@ class Plan:
 
     def launch_plain(self, stream=None):
         check(lib().lrb_launch_plain(self.ptr, _stream_ptr(stream)))
+
+    def status(self) -> int:
+        """lrb_plan_status: synchronises and reports an expired device wait."""
+        return lib().lrb_plan_status(self.ptr)
+
+    def dump_levels(self, dump_ptr: int, stream=None):
+        check(lib().lrb_split_dump_levels(self.ptr, ctypes.c_void_p(dump_ptr), _stream_ptr(stream)))
 
     def info(self) -> dict:
         i = lrb_plan_info()

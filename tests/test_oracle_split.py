@@ -146,3 +146,20 @@ def test_more_digits_more_accuracy():
     for a, b in zip(errs, errs[1:]):
         assert b < a * 2.0 ** -5          # each digit buys ~beta bits
     assert errs[-1] < 1e-11            # triangular truncation dominates at S = 5
+
+
+@pytest.mark.parametrize("name", sorted(PRESETS))
+def test_element_sampler_matches_full_oracle(name):
+    p = PRESETS[name]
+    rng = np.random.default_rng(12)
+    m, n, k = 7, 6, 2 * p.kc + 3
+    A = rng.standard_normal((m, k)) * 10.0 ** rng.uniform(-4, 4, (m, k))
+    B = rng.standard_normal((k, n)) * 10.0 ** rng.uniform(-4, 4, (k, n))
+    C = rng.standard_normal((m, n))
+    full = oracle.split_gemm(A, B, C, p)
+    I, J = np.meshgrid(np.arange(m), np.arange(n), indexing="ij")
+    I, J = I.ravel(), J.ravel()
+    got = oracle.split_dot_samples(A[I, :], B[:, J].T, C[I, J], p)
+    assert np.array_equal(got, full[I, J])
+    mag = oracle.recombination_magnitude(A, B, C, p)
+    assert np.all(mag >= np.abs(full) * (1 - 1e-12))
