@@ -180,6 +180,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other workloads (64-entry O-form, variable-size, split precision, serving)")
+    ap.add_argument("--extras", default="small,variable,split,serving,dmma",
+                    help="comma-separated subset of the other workloads to run")
+    ap.add_argument("--split-batch", type=int, default=2048, help="entries of the split-precision batch")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="batch-count scale of every group (profiling runs use a small case)")
     args = ap.parse_args()
@@ -290,12 +295,20 @@ def main():
     if not args.no_e2e:
         line["e2e"] = e2e_leg(L, handle, batches, flops, args, barrier, max_over_ranks, world, stream)
 
+    if not args.no_extras and world == 1:
+        plan.close()
+        plan = None
+        del batches
+        torch.cuda.empty_cache()
+        line["extras"] = extras(L, handle, stream, dev, peak, timed, set(args.extras.split(",")), args.split_batch)
+
     if not args.no_cpu and rank == 0 and world == 1:
         f, s, used, ents = cpu_baseline(args.cpu_fraction)
         line["cpu_baseline"] = {"value": round(f / s / 1e9, 3), "unit": UNIT, "cores": used, "kind": "oracle",
                                 "sample": (f"first {args.cpu_fraction:.3g} of every group of the sweep "
                                            f"({ents} entries, {f:.3g} flops, {s:.1f} s on the host cores)")}
-    plan.close()
+    if plan is not None:
+        plan.close()
     handle.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -304,26 +317,240 @@ def main():
     return 0
 
 
+def extras(L, handle, stream, dev, peak_fp64, timed, which, split_batch):
+    """The other workloads, each with its own plan, 3 warm-up and 5 timed launches:
+    the 64-entry O-form batch (L2 flushed before every launch: it fits in L2),
+    the 20,000-entry variable-size batch (persistent vs one launch per shape),
+    and the split-precision batch (b 1024, r 64, 2048 entries, 10^U(-4,4) N(0,1))."""
+    import torch
+    from paper_2311_07602_gb300 import workloads as W
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    out = {}
+
+    if "small" in which:
+        out["small_o_form"] = small_leg(L, handle, stream, dev, peak_fp64)
+    if "variable" in which:
+        out["variable_size"] = variable_leg(L, handle, dev, peak_fp64, timed)
+    if "split" in which:
+        out["split"] = split_leg(L, handle, dev, timed, hbm, split_batch)
+    if "serving" in which:
+        out["serving"] = serving_leg(L, handle, dev, peak_fp64)
+    if "dmma" in which:
+        out["dmma"] = dmma_leg(L, handle, dev, peak_fp64, timed)
+    return out
+
+
+def dmma_leg(L, handle, dev, peak_fp64, timed, scale=0.25):
+    """FP64 tensor-core (DMMA) tiles against DFMA tiles on a quarter of the
+    uniform sweep: tuned without DMMA, tuned with DMMA allowed (the tuner
+    keeps a DMMA tile only where it measures faster), and DMMA forced."""
+    import torch
+    batches = sweep_batches(dev, scale)
+    descs = np.concatenate([L.descs_for(b) for b in batches])
+    f = float(sum(b.flops() for b in batches))
+    out = {"workload": f"uniform sweep, batch counts x {scale}"}
+    for name, opts in (("dfma_tuned", {}), ("dmma_allowed_tuned", {"precision": L.LRB_PREC_FP64_DMMA_ALLOWED}),
+                       ("dmma_forced_64x32", {"force_variant": 8})):
+        with handle.plan(descs, use_graph=True, **opts) as p:
+            info = p.info()
+            ms, _ = timed(lambda s: p.launch(s), 3, 3)
+        out[name] = {"gflops": round(f * 3 / ms / 1e6, 1), "frac_fp64_peak": round(f * 3 / ms / 1e9 / peak_fp64, 4),
+                     "dmma_tiles": int(info["dmma_items"]), "tiles": int(info["items"])}
+    del batches
+    torch.cuda.empty_cache()
+    return out
+
+
+def small_leg(L, handle, stream, dev, peak_fp64):
+    """64-entry O-form, C(256x256) += A(256x16) B(16x256), U[-1,1], seed 0;
+    it fits in L2, so a 256 MB buffer is written before every launch."""
+    import torch
+    from paper_2311_07602_gb300 import workloads as W
+    b = W.small_o_form(device=dev)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MB > L2
+    with handle.plan(L.descs_for(b), use_graph=True) as p:
+        per = []
+        for i in range(8):
+            flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            p.launch(stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i >= 3:
+                per.append(e0.elapsed_time(e1))
+    f = b.flops()
+    ms = statistics.median(per)
+    return {"workload": "O-form, 64 x C(256x256) += A(256x16) B(16x256), U[-1,1], seed 0, L2 flushed",
+            "gflops": round(f / ms / 1e6, 2), "ms": round(ms, 4), "frac_fp64_peak": round(f / ms / 1e9 / peak_fp64, 4)}
+
+
+def variable_leg(L, handle, dev, peak_fp64, timed):
+    """20,000 entries, b log-uniform [64, 2048], r in {8..128}, T/O 50/50:
+    one persistent graph launch against one launch per distinct shape."""
+    import torch
+    from paper_2311_07602_gb300 import workloads as W
+    forms, bs, rs = W.variable_shapes(20000, seed=3)
+    vb = W.variable_batch(forms, bs, rs, seed=3, device=dev, pool_elems=(4 << 30) // 8)
+    t0 = time.perf_counter()
+    p = handle.plan(L.descs_for(vb), use_graph=True)
+    plan_s = time.perf_counter() - t0
+    info = p.info()
+    f = vb.flops()
+    ms_p, _ = timed(lambda s: p.launch(s), 5, 3)
+    ms_q, _ = timed(lambda s: p.launch_plain(s), 5, 3)
+    out = {
+        "workload": "20,000 entries, b log-uniform [64,2048], r in {8,16,32,64,128}, T/O 50/50, N(0,1), seed 3, "
+                    "A/B views into a 4 GB pool",
+        "flops": f, "persistent_gflops": round(f * 5 / ms_p / 1e6, 2), "plain_gflops": round(f * 5 / ms_q / 1e6, 2),
+        "vs_plain": round(ms_q / ms_p, 4), "frac_fp64_peak": round(f * 5 / ms_p / 1e9 / peak_fp64, 4),
+        "persistent_ms": round(ms_p / 5, 3), "plain_ms": round(ms_q / 5, 3), "plain_launches": int(info["groups"]),
+        "tiles": int(info["items"]), "plan_s_incl_tuning": round(plan_s, 2)}
+    p.close()
+    del vb
+    torch.cuda.empty_cache()
+    return out
+
+
+def split_leg(L, handle, dev, timed, hbm, batch):
+    """Split precision (BF16/FP16 x 3/4 digits) against the FP64 path on the
+    wide-range batch b 1024, r 64, entries 10^U(-4,4) N(0,1), both forms."""
+    import torch
+    from paper_2311_07602_gb300 import workloads as W
+    res = {}
+    for form in (W.FORM_T, W.FORM_O):
+        wb = W.wide_range(form, batch=batch, device=dev)
+        f = wb.flops()
+        ab = wb.alg_bytes()
+        row = {}
+        for name, prec in (("fp64", L.LRB_PREC_FP64), ("bf16_s3", L.LRB_PREC_SPLIT_BF16_S3),
+                           ("bf16_s4", L.LRB_PREC_SPLIT_BF16_S4), ("fp16_s3", L.LRB_PREC_SPLIT_FP16_S3),
+                           ("fp16_s4", L.LRB_PREC_SPLIT_FP16_S4)):
+            with handle.plan(L.descs_for(wb), precision=prec, use_graph=(prec == L.LRB_PREC_FP64)) as p:
+                steps = 2 if prec == L.LRB_PREC_FP64 else 5
+                ms, _ = timed(lambda s: p.launch(s), steps, 3)
+                st = p.status()
+            ms /= steps
+            row[name] = {"ms": round(ms, 3), "gflops_fp64_equiv": round(f / ms / 1e6, 1),
+                         "hbm_gbs_alg": round(ab / ms / 1e6, 1), "frac_hbm": round(ab / ms / 1e6 / hbm, 4),
+                         "status": int(st)}
+        res["T" if form == W.FORM_T else "O"] = row
+        del wb
+        torch.cuda.empty_cache()
+    return {"workload": f"b 1024, r 64, {batch} entries, 10^U(-4,4) N(0,1), seed 4", "hbm_peak_gbs": hbm, **res}
+
+
+def serving_leg(L, handle, dev, peak_fp64, budget=40 << 30):
+    """Poisson request streams into the continuous-batching queue.  Each
+    request: 1..512 products, b log-uniform [64, 2048], r in {8..128}, T/O
+    50/50; operands are views into a 4 GB device pool, results go to a 64 GB
+    device ring.  Offered loads: 0.25 / 0.5 / 0.75 / 0.9 x the FP64 capacity
+    (FP64 peak / mean request flops) for 3 s each, and the stated overload
+    rates 1,000 and 20,000 req/s for 0.5 s each (waiting FIFO limited to 32
+    so the backlog drains quickly); 40 GB admission budget, 4 stream slots."""
+    import torch
+    from paper_2311_07602_gb300 import workloads as W
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    pool = torch.empty((4 << 30) // 8, dtype=torch.float64, device=dev).normal_(generator=g)
+    ring = torch.zeros((64 << 30) // 8, dtype=torch.float64, device=dev)
+    _, probe = W.serving_requests(2000, 1.0, seed=55)
+    mean_flops = float(np.mean([np.sum(2.0 * bb.astype(np.float64) ** 2 * rr) for _, bb, rr in probe]))
+    capacity = 0.98 * peak_fp64 * 1e12 / mean_flops
+    points = [(f"{fr:g}x capacity", fr * capacity, 3.0, 4096) for fr in (0.25, 0.5, 0.75, 0.9)]
+    points += [("1k req/s", 1000.0, 0.5, 32), ("20k req/s", 20000.0, 0.5, 32)]
+    rng = np.random.default_rng(505)
+    cursor = 0
+    results = []
+    for idx, (label, rate, secs, max_waiting) in enumerate(points):
+        count = max(4, int(rate * secs))
+        arrivals, reqs = W.serving_requests(count, rate, seed=500 + idx)
+        descs = []
+        for forms, bs, rs in reqs:
+            m = bs.astype(np.int64)
+            n = np.where(forms == W.FORM_T, rs, bs).astype(np.int64)
+            k = np.where(forms == W.FORM_T, bs, rs).astype(np.int64)
+            d = np.zeros(len(bs), dtype=L.DESC_DTYPE)
+            offa = rng.integers(0, (pool.numel() - m * k) // 32) * 32
+            offb = rng.integers(0, (pool.numel() - k * n) // 32) * 32
+            sizes = ((m * n + 31) // 32) * 32
+            need = int(sizes.sum())
+            if cursor + need > ring.numel():
+                cursor = 0
+            offc = cursor + np.concatenate([[0], np.cumsum(sizes)[:-1]])
+            cursor += need
+            d["A"] = np.uint64(pool.data_ptr()) + 8 * offa.astype(np.uint64)
+            d["B"] = np.uint64(pool.data_ptr()) + 8 * offb.astype(np.uint64)
+            d["C"] = np.uint64(ring.data_ptr()) + 8 * offc.astype(np.uint64)
+            d["m"], d["n"], d["k"] = m, n, k
+            d["lda"], d["ldb"], d["ldc"] = m, k, m
+            descs.append(d)
+        torch.cuda.synchronize()
+        q = L.Queue(handle, budget, max_inflight=4)
+        q.set_limits(max_waiting)
+        tickets, codes = [], {}
+        t0 = time.perf_counter()
+        for t_arr, d in zip(arrivals, descs):
+            while time.perf_counter() - t0 < t_arr:
+                pass
+            st, tk = q.submit(d)
+            codes[st] = codes.get(st, 0) + 1
+            if st == L.LRB_OK:
+                tickets.append(tk)
+        submit_s = time.perf_counter() - t0
+        for tk in tickets:
+            q.wait(tk, 300000)
+        st = q.stats()
+        q.close()
+        results.append({"load": label, "offered_req_s": round(rate, 2), "duration_s": round(submit_s, 3),
+                        "submitted": count, "accepted": int(st["accepted"]),
+                        "rejected_queue_full": int(st["rejected_full"]), "rejected_budget": int(st["rejected_budget"]),
+                        "completed": int(st["completed"]), "p50_ms": round(st["p50_ms"], 3),
+                        "p99_ms": round(st["p99_ms"], 3), "sustained_gflops": round(st["gflops"], 1),
+                        "waves": int(st["waves"]), "max_concurrent_waves": int(st["max_concurrent_waves"]),
+                        "mean_wave_entries": round(st["mean_wave_entries"], 1),
+                        "peak_reserved_gb": round(st["peak_reserved_bytes"] / 1e9, 2)})
+    del pool, ring
+    torch.cuda.empty_cache()
+    return {"workload": "Poisson requests, 1..512 products each, b log-uniform [64,2048], r in {8..128}, "
+                        "T/O 50/50, N(0,1), FP64, 40 GB budget, 4 stream slots",
+            "mean_request_gflop": round(mean_flops / 1e9, 2), "capacity_req_s": round(capacity, 1),
+            "points": results}
+
+
 def e2e_leg(L, handle, batches, flops, args, barrier, max_over_ranks, world, stream):
     """Same workload through lrb_execute_host: inputs in pinned host memory,
     host->device copies, the launch and the device->host copy of every C in
-    the timed region."""
+    the timed region.  With N ranks every rank takes the first 1/N of each
+    group (host memory is shared by the ranks), and flops count what ran."""
     import torch
-    host = []
     rows = []
+    hold = []
     h2d = d2h = 0
+    fl = 0.0
     for b in batches:
-        A = torch.empty(b.A.numel(), dtype=torch.float64, pin_memory=True)
-        B = torch.empty(b.B.numel(), dtype=torch.float64, pin_memory=True)
-        C = torch.empty(b.C.numel(), dtype=torch.float64, pin_memory=True)
-        A.copy_(b.A)
-        B.copy_(b.B)
-        C.copy_(b.C)
-        host.append((A, B, C))
-        d = L.descs_for(type(b)(A, B, C, b.m, b.n, b.k, b.lda, b.ldb, b.ldc, b.offA, b.offB, b.offC))
-        rows.append(d)
+        cnt = max(1, len(b) // world)
+        ea, eb, ec = (int(b.offA[cnt - 1] + b.lda[cnt - 1] * b.k[cnt - 1]), int(b.offB[cnt - 1] + b.ldb[cnt - 1] *
+                      b.n[cnt - 1]), int(b.offC[cnt - 1] + b.ldc[cnt - 1] * b.n[cnt - 1]))
+        A = torch.empty(ea, dtype=torch.float64, pin_memory=True)
+        B = torch.empty(eb, dtype=torch.float64, pin_memory=True)
+        C = torch.empty(ec, dtype=torch.float64, pin_memory=True)
+        A.copy_(b.A[:ea])
+        B.copy_(b.B[:eb])
+        C.copy_(b.C[:ec])
+        hold.append((A, B, C))
+        sub = type(b)(A, B, C, b.m[:cnt], b.n[:cnt], b.k[:cnt], b.lda[:cnt], b.ldb[:cnt], b.ldc[:cnt], b.offA[:cnt],
+                      b.offB[:cnt], b.offC[:cnt])
+        rows.append(L.descs_for(sub))
         h2d += 8 * (A.numel() + B.numel() + C.numel())
         d2h += 8 * C.numel()
+        fl += sub.flops()
     descs = np.concatenate(rows)
     torch.cuda.synchronize()
     for _ in range(args.warmup):
@@ -336,10 +563,11 @@ def e2e_leg(L, handle, batches, flops, args, barrier, max_over_ranks, world, str
     torch.cuda.synchronize()
     barrier()
     secs = max_over_ranks(time.perf_counter() - t0)
-    del host
-    return {"value": round(world * flops * args.e2e_steps / secs / 1e9, 2), "unit": UNIT,
+    del hold
+    return {"value": round(world * fl * args.e2e_steps / secs / 1e9, 2), "unit": UNIT,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps,
-            "api": "lrb_execute_host (pinned host buffers)"}
+            "flops_per_step_per_rank": fl,
+            "api": "lrb_execute_host (pinned host buffers; copies in, compute and copies out pipelined in pieces)"}
 
 
 if __name__ == "__main__":

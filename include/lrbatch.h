@@ -96,6 +96,7 @@ typedef struct lrb_plan_info {
     double alg_bytes;       /* sum of 8 (m k + k n + 2 m n): each operand once, C read and written */
     int32_t grid;           /* CTAs of the persistent launch */
     int32_t precision;
+    int64_t dmma_items;     /* tiles that run on FP64 tensor-core (DMMA) variants */
 } lrb_plan_info;
 
 /* ---- handle -------------------------------------------------------------
@@ -139,7 +140,7 @@ lrb_status lrb_plan_status(lrb_plan* p);
  * (C += A B as lrb_launch does) and also writes every k-chunk's FP32 level
  * sums P_L (the tensor-core accumulators before recombination) to the
  * device array `dump` laid out as float[chunks][S][m][n], chunks =
- * ceil(k / kc) (kc = 128 for BF16, 32 for FP16), level L = index + 2.
+ * ceil(k / kc) (kc = 64 for BF16, 32 for FP16), level L = index + 2.
  * LRB_ERR_UNSUPPORTED for FP64 plans or plans of several entries. */
 lrb_status lrb_split_dump_levels(lrb_plan* p, float* dump, void* stream);
 
@@ -196,6 +197,45 @@ lrb_status lrb_variant_shape(int32_t variant, int32_t* bm, int32_t* bn, int32_t*
 #define LRB_NOALLOC_MAX_ENTRIES 4096
 #define LRB_NOALLOC_MAX_TILES 262144
 lrb_status lrb_launch_noalloc(const lrb_gemm_desc* host_descs, size_t count, void* stream);
+
+/* ---- serving queue --------------------------------------------------------
+ * Continuous batching of multiplication requests (not in the paper, which
+ * runs one batch at a time).  A request is a host array of descriptors
+ * (device operands, caller-owned, valid until the request completes).
+ * lrb_queue_submit is non-blocking: LRB_OK (queued; *ticket set),
+ * LRB_ERR_INVALID (bad descriptors), LRB_ERR_BUDGET (the request alone needs
+ * more than hbm_budget_bytes: 8 (m k + k n + m n) + 64 bytes per entry) or
+ * LRB_ERR_QUEUE_FULL (the waiting FIFO is at its limit: back-pressure).  A
+ * worker thread admits waiting requests in FIFO order while their bytes fit
+ * in the budget left, launches each wave as one persistent launch on one of
+ * `max_inflight` (1..16) stream slots, so waves that arrive while others run
+ * overlap on the device, and retires finished waves, releasing their budget.
+ * Results are bitwise the same alone or mixed with other requests. */
+typedef struct lrb_queue_stats_t {
+    uint64_t accepted, rejected_budget, rejected_full, rejected_invalid;
+    uint64_t completed, failed, waiting, waves, max_concurrent_waves;
+    double mean_wave_entries;
+    uint64_t reserved_bytes, peak_reserved_bytes, budget_bytes;
+    double p50_ms, p99_ms, mean_ms, max_ms;   /* submission -> completion observed */
+    double gflops;                            /* completed flops / (last completion - first submission) */
+    double flops_done;
+} lrb_queue_stats_t;
+
+lrb_status lrb_queue_create(lrb_handle* h, size_t hbm_budget_bytes, int max_inflight, lrb_queue** out);
+/* Waiting-FIFO limit (default 4096 requests) and entries per wave (default
+ * 65536; a larger request still forms a wave of its own). */
+lrb_status lrb_queue_set_limits(lrb_queue* q, size_t max_waiting, size_t max_wave_entries);
+lrb_status lrb_queue_submit(lrb_queue* q, const lrb_gemm_desc* host_descs, size_t n, uint64_t* ticket);
+/* LRB_OK when done, LRB_ERR_TIMEOUT while pending, LRB_ERR_DEVICE if it failed. */
+lrb_status lrb_queue_poll(lrb_queue* q, uint64_t ticket);
+/* Bounded wait (timeout_ms < 0 means 600 s): LRB_OK, LRB_ERR_TIMEOUT or LRB_ERR_DEVICE. */
+lrb_status lrb_queue_wait(lrb_queue* q, uint64_t ticket, int timeout_ms);
+/* Latency of a completed request (submission -> completion observed), ms. */
+lrb_status lrb_queue_latency(lrb_queue* q, uint64_t ticket, double* latency_ms);
+lrb_status lrb_queue_stats(lrb_queue* q, lrb_queue_stats_t* out);
+/* Drains the queue (bounded by timeout_ms; < 0 means 600 s), stops the
+ * worker and frees everything; LRB_ERR_TIMEOUT if it had to abandon work. */
+lrb_status lrb_queue_destroy(lrb_queue* q, int timeout_ms);
 
 /* Message of the last failure on the calling thread ("" if none). */
 const char* lrb_last_error(void);

@@ -67,8 +67,8 @@ class SplitParams:
 # The four configurations of the split path (BF16/FP16 x 3/4 digits).  The
 # chunk lengths keep every level sum within 2^24 (see level_bound below).
 PRESETS = {
-    "bf16_s3": SplitParams("bf16", 8, 3, 128),
-    "bf16_s4": SplitParams("bf16", 8, 4, 128),
+    "bf16_s3": SplitParams("bf16", 8, 3, 64),
+    "bf16_s4": SplitParams("bf16", 8, 4, 64),
     "fp16_s3": SplitParams("fp16", 9, 3, 32),
     "fp16_s4": SplitParams("fp16", 9, 4, 32),
 }

@@ -207,8 +207,11 @@ struct lrb_handle {
     void* arena = nullptr;
     size_t arena_bytes = 0;
     std::vector<lrb_gemm_desc> host_key;
+    std::vector<size_t> host_cut;
     lrb_plan_opts host_opts{};
-    lrb_plan* host_plan = nullptr;
+    std::vector<lrb_plan*> host_plans;
+    cudaStream_t copy_in = nullptr, copy_out = nullptr;
+    std::vector<cudaEvent_t> ev_in, ev_done;
 };
 
 struct lrb_plan {
@@ -412,6 +415,22 @@ void free_plan(lrb_plan* p) {
 
 void lrb::set_last_error(const char* msg) { g_err = msg; }
 
+// Planner pieces shared with the serving queue (serve.cu).
+lrb_status lrb::validate_descs(const lrb_gemm_desc* d, size_t count, const lrb_plan_opts& o) {
+    return validate(d, count, o);
+}
+lrb_status lrb::plan_variants(lrb_handle* h, const lrb_gemm_desc* d, size_t count, const lrb_plan_opts& o,
+                              std::vector<int>& var) {
+    return choose_variants(h, d, count, o, var);
+}
+void lrb::plan_tiles(const lrb_gemm_desc* d, size_t count, const std::vector<int>& var, std::vector<Item>& items) {
+    make_tiles(d, count, var, items);
+}
+lrb::HandleInfo lrb::handle_info(const lrb_handle* h) {
+    return HandleInfo{h->device, h->sms, h->blocks_per_sm, h->blocks_per_sm_wide};
+}
+lrb_plan_opts lrb::default_plan_opts() { return default_opts(); }
+
 extern "C" {
 
 const char* lrb_last_error(void) { return g_err.c_str(); }
@@ -501,7 +520,11 @@ lrb_status lrb_destroy(lrb_handle* h) {
     if (!h) return fail(LRB_ERR_INVALID, "handle is NULL");
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
-    if (h->host_plan) free_plan(h->host_plan);
+    for (lrb_plan* p : h->host_plans) free_plan(p);
+    for (cudaEvent_t e : h->ev_in) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->ev_done) cudaEventDestroy(e);
+    if (h->copy_in) cudaStreamDestroy(h->copy_in);
+    if (h->copy_out) cudaStreamDestroy(h->copy_out);
     if (h->arena) cudaFree(h->arena);
     if (h->scratch) cudaFree(h->scratch);
     if (h->stream) cudaStreamDestroy(h->stream);
@@ -615,6 +638,8 @@ lrb_status lrb_plan_create(lrb_handle* h, const lrb_gemm_desc* host_descs, size_
         if (!variant_is_narrow(var[e])) p->wide = true;
     p->grid = std::max(1, std::min(h->sms * (p->wide ? h->blocks_per_sm_wide : h->blocks_per_sm), p->n_items));
     p->info.items = p->n_items;
+    p->info.dmma_items = 0;
+    for (const Item& it : items) p->info.dmma_items += kVariants[it.variant].dmma ? 1 : 0;
     p->info.groups = (int64_t)p->groups.size();
     p->info.grid = p->grid;
 
@@ -677,9 +702,33 @@ lrb_status lrb_execute_host(lrb_handle* h, const lrb_gemm_desc* host_descs, size
     LRB_CUDA(cudaSetDevice(h->device));
     cudaStream_t s = (cudaStream_t)stream;
 
-    // Device layout: A blocks, then B blocks, then C blocks, each packed with
-    // ld = rows.  An A or B block whose (pointer, rows, cols, ld) repeats an
-    // earlier one is shared.
+    // Pieces: contiguous entry ranges of about equal bytes (at most 8, at
+    // least 64 MB each).  Piece p's copies in, its launch and its copies out
+    // run on three streams joined by events, so piece p+1 moves in while p
+    // computes and p-1 moves out.
+    std::vector<double> eb(count);
+    double total = 0;
+    for (size_t e = 0; e < count; ++e) {
+        const lrb_gemm_desc& x = host_descs[e];
+        eb[e] = 8.0 * ((double)x.m * x.k + (double)x.k * x.n + 2.0 * x.m * x.n);
+        total += eb[e];
+    }
+    const int npieces = (int)std::max(1.0, std::min(8.0, std::floor(total / (64.0 * (1 << 20)))));
+    std::vector<size_t> cut(1, 0);
+    {
+        double acc = 0;
+        for (size_t e = 0; e < count; ++e) {
+            acc += eb[e];
+            if ((int)cut.size() < npieces && acc >= total * (double)cut.size() / npieces && e + 1 < count)
+                cut.push_back(e + 1);
+        }
+        cut.push_back(count);
+    }
+    const int P = (int)cut.size() - 1;
+
+    // Device layout: piece by piece, A blocks then B blocks then C blocks,
+    // each packed with ld = rows.  An A or B block whose (pointer, rows,
+    // cols, ld) repeats an earlier one is shared (copied by the first piece).
     struct Copy {
         const double* host;
         size_t dev;        // element offset in the arena
@@ -687,58 +736,53 @@ lrb_status lrb_execute_host(lrb_handle* h, const lrb_gemm_desc* host_descs, size
         size_t elems;      // contiguous run length (tight blocks)
     };
     std::vector<lrb_gemm_desc> dd(host_descs, host_descs + count);
-    std::vector<Copy> h2d, d2h;
+    std::vector<std::vector<Copy>> h2d(P), d2h(P);
+    std::vector<size_t> wa(count), wb(count), wc(count);
+    std::map<std::tuple<uintptr_t, int, int, int>, size_t> seen;
     size_t cursor = 0;
-    auto place = [&](int cls, std::vector<size_t>& where) {
-        std::map<std::tuple<uintptr_t, int, int, int>, size_t> seen;
-        where.resize(count);
-        const size_t cls_start = h2d.size();   // runs never merge across operand classes
-        for (size_t e = 0; e < count; ++e) {
-            const lrb_gemm_desc& x = host_descs[e];
-            const double* p = cls == 0 ? x.A : cls == 1 ? x.B : x.C;
-            const int rows = cls == 0 ? x.m : cls == 1 ? x.k : x.m;
-            const int cols = cls == 0 ? x.k : cls == 1 ? x.n : x.n;
-            const int ld = cls == 0 ? x.lda : cls == 1 ? x.ldb : x.ldc;
-            const auto key = std::make_tuple((uintptr_t)p, rows, cols, ld);
-            if (cls < 2) {
-                auto it = seen.find(key);
-                if (it != seen.end()) {
-                    where[e] = it->second;
-                    continue;
+    for (int pc = 0; pc < P; ++pc) {
+        for (int cls = 0; cls < 3; ++cls) {
+            std::vector<Copy>& list = h2d[pc];
+            const size_t cls_start = list.size();   // runs never merge across operand classes
+            for (size_t e = cut[pc]; e < cut[pc + 1]; ++e) {
+                const lrb_gemm_desc& x = host_descs[e];
+                const double* ptr = cls == 0 ? x.A : cls == 1 ? x.B : x.C;
+                const int rows = cls == 0 ? x.m : cls == 1 ? x.k : x.m;
+                const int cols = cls == 0 ? x.k : cls == 1 ? x.n : x.n;
+                const int ld = cls == 0 ? x.lda : cls == 1 ? x.ldb : x.ldc;
+                std::vector<size_t>& where = cls == 0 ? wa : cls == 1 ? wb : wc;
+                if (cls < 2) {
+                    auto it = seen.find(std::make_tuple((uintptr_t)ptr, rows, cols, ld));
+                    if (it != seen.end()) {
+                        where[e] = it->second;
+                        continue;
+                    }
+                    seen[std::make_tuple((uintptr_t)ptr, rows, cols, ld)] = cursor;
                 }
-            }
-            const size_t elems = (size_t)rows * cols;
-            where[e] = cursor;
-            if (cls < 2) seen[key] = cursor;
-            Copy c{p, cursor, rows, cols, ld, elems};
-            std::vector<Copy>& list = h2d;
-            if (list.size() > cls_start && ld == rows) {
-                Copy& b = list.back();
-                if (b.ld == b.rows && b.host + b.elems == p && b.dev + b.elems == cursor) {
-                    b.elems += elems;
-                    b.cols = -1;   // merged run: a 1-D copy
+                const size_t elems = (size_t)rows * cols;
+                where[e] = cursor;
+                Copy c{ptr, cursor, rows, cols, ld, elems};
+                if (list.size() > cls_start && ld == rows) {
+                    Copy& b = list.back();
+                    if (b.ld == b.rows && b.host + b.elems == ptr && b.dev + b.elems == cursor) {
+                        b.elems += elems;
+                        b.cols = -1;   // merged run: a 1-D copy
+                    } else {
+                        list.push_back(c);
+                    }
                 } else {
                     list.push_back(c);
                 }
-            } else {
-                list.push_back(c);
+                cursor += elems;
             }
-            cursor += elems;
+            if (cls == 2) d2h[pc].assign(list.begin() + cls_start, list.end());
         }
-    };
-    std::vector<size_t> wa, wb, wc;
-    place(0, wa);
-    place(1, wb);
-    const size_t c_first = h2d.size();
-    place(2, wc);
-    d2h.assign(h2d.begin() + c_first, h2d.end());
+    }
 
     const size_t need = cursor * 8 + 256;
     if (need > h->arena_bytes) {
-        if (h->host_plan) {
-            free_plan(h->host_plan);
-            h->host_plan = nullptr;
-        }
+        for (lrb_plan* p : h->host_plans) free_plan(p);
+        h->host_plans.clear();
         cudaStreamSynchronize(s);
         if (h->arena) cudaFree(h->arena);
         h->arena = nullptr;
@@ -747,6 +791,17 @@ lrb_status lrb_execute_host(lrb_handle* h, const lrb_gemm_desc* host_descs, size
         if (ce != cudaSuccess) return fail(LRB_ERR_NOMEM, std::string("host-run arena: ") + cudaGetErrorString(ce));
         h->arena_bytes = need;
         h->host_key.clear();
+    }
+    if (!h->copy_in) {
+        LRB_CUDA(cudaStreamCreateWithFlags(&h->copy_in, cudaStreamNonBlocking));
+        LRB_CUDA(cudaStreamCreateWithFlags(&h->copy_out, cudaStreamNonBlocking));
+    }
+    while ((int)h->ev_in.size() < P) {
+        cudaEvent_t a, b;
+        LRB_CUDA(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+        LRB_CUDA(cudaEventCreateWithFlags(&b, cudaEventDisableTiming));
+        h->ev_in.push_back(a);
+        h->ev_done.push_back(b);
     }
     double* base = (double*)h->arena;
     for (size_t e = 0; e < count; ++e) {
@@ -757,38 +812,57 @@ lrb_status lrb_execute_host(lrb_handle* h, const lrb_gemm_desc* host_descs, size
         dd[e].ldb = dd[e].k;
         dd[e].ldc = dd[e].m;
     }
-    const bool same = h->host_plan && h->host_key.size() == count &&
+    const bool same = !h->host_plans.empty() && h->host_key.size() == count && h->host_cut == cut &&
                       std::memcmp(h->host_key.data(), dd.data(), sizeof(lrb_gemm_desc) * count) == 0 &&
                       std::memcmp(&h->host_opts, &o, sizeof(o)) == 0;
     if (!same) {
-        if (h->host_plan) {
-            cudaStreamSynchronize(s);
-            free_plan(h->host_plan);
-            h->host_plan = nullptr;
+        cudaStreamSynchronize(s);
+        for (lrb_plan* p : h->host_plans) free_plan(p);
+        h->host_plans.clear();
+        for (int pc = 0; pc < P; ++pc) {
+            lrb_plan* p = nullptr;
+            lrb_plan_opts po = o;
+            po.check_alias = 0;   // checked above on the caller's host ranges
+            st = lrb_plan_create(h, dd.data() + cut[pc], cut[pc + 1] - cut[pc], &po, &p);
+            if (st != LRB_OK) {
+                for (lrb_plan* q : h->host_plans) free_plan(q);
+                h->host_plans.clear();
+                return st;
+            }
+            h->host_plans.push_back(p);
         }
-        lrb_plan* p = nullptr;
-        st = lrb_plan_create(h, dd.data(), count, &o, &p);
-        if (st != LRB_OK) return st;
-        h->host_plan = p;
         h->host_key = dd;
+        h->host_cut = cut;
         h->host_opts = o;
     }
-    auto copy = [&](const Copy& c, bool to_dev) -> cudaError_t {
+    auto copy = [&](const Copy& c, bool to_dev, cudaStream_t cs) -> cudaError_t {
         double* dptr = base + c.dev;
         if (c.cols < 0 || c.ld == c.rows) {
             const size_t bytes = c.elems * 8;
-            return to_dev ? cudaMemcpyAsync(dptr, c.host, bytes, cudaMemcpyHostToDevice, s)
-                          : cudaMemcpyAsync((void*)c.host, dptr, bytes, cudaMemcpyDeviceToHost, s);
+            return to_dev ? cudaMemcpyAsync(dptr, c.host, bytes, cudaMemcpyHostToDevice, cs)
+                          : cudaMemcpyAsync((void*)c.host, dptr, bytes, cudaMemcpyDeviceToHost, cs);
         }
         return to_dev ? cudaMemcpy2DAsync(dptr, (size_t)c.rows * 8, c.host, (size_t)c.ld * 8, (size_t)c.rows * 8,
-                                          c.cols, cudaMemcpyHostToDevice, s)
+                                          c.cols, cudaMemcpyHostToDevice, cs)
                       : cudaMemcpy2DAsync((void*)c.host, (size_t)c.ld * 8, dptr, (size_t)c.rows * 8,
-                                          (size_t)c.rows * 8, c.cols, cudaMemcpyDeviceToHost, s);
+                                          (size_t)c.rows * 8, c.cols, cudaMemcpyDeviceToHost, cs);
     };
-    for (const Copy& c : h2d) LRB_CUDA(copy(c, true));
-    st = lrb_launch(h->host_plan, stream);
-    if (st != LRB_OK) return st;
-    for (const Copy& c : d2h) LRB_CUDA(copy(c, false));
+    // the copy streams start after work already queued on the caller's stream
+    LRB_CUDA(cudaEventRecord(h->ev_done[0], s));
+    LRB_CUDA(cudaStreamWaitEvent(h->copy_in, h->ev_done[0], 0));
+    for (int pc = 0; pc < P; ++pc) {
+        for (const Copy& c : h2d[pc]) LRB_CUDA(copy(c, true, h->copy_in));
+        LRB_CUDA(cudaEventRecord(h->ev_in[pc], h->copy_in));
+    }
+    for (int pc = 0; pc < P; ++pc) {
+        LRB_CUDA(cudaStreamWaitEvent(s, h->ev_in[pc], 0));
+        st = lrb_launch(h->host_plans[pc], stream);
+        if (st != LRB_OK) return st;
+        LRB_CUDA(cudaEventRecord(h->ev_done[pc], s));
+        LRB_CUDA(cudaStreamWaitEvent(h->copy_out, h->ev_done[pc], 0));
+        for (const Copy& c : d2h[pc]) LRB_CUDA(copy(c, false, h->copy_out));
+    }
+    LRB_CUDA(cudaStreamSynchronize(h->copy_out));
     LRB_CUDA(cudaStreamSynchronize(s));
     return LRB_OK;
 }

@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 #include "../../include/lrbatch.h"
 
@@ -59,5 +60,18 @@ bool variant_is_narrow(int v);
 
 // Sets the calling thread's lrb_last_error() message (api.cu).
 void set_last_error(const char* msg);
+
+// Planner pieces (api.cu) used by the serving queue.
+struct HandleInfo {
+    int device, sms, blocks_per_sm, blocks_per_sm_wide;
+};
+HandleInfo handle_info(const lrb_handle* h);
+lrb_plan_opts default_plan_opts();
+lrb_status validate_descs(const lrb_gemm_desc* d, size_t count, const lrb_plan_opts& o);
+// Tile variant per entry (tuned-cache lookup, else tuning or the heuristic as o.tune says).
+lrb_status plan_variants(lrb_handle* h, const lrb_gemm_desc* d, size_t count, const lrb_plan_opts& o,
+                         std::vector<int>& var);
+// Output tiles of all entries, longest first.
+void plan_tiles(const lrb_gemm_desc* d, size_t count, const std::vector<int>& var, std::vector<Item>& items);
 
 }  // namespace lrb

@@ -14,23 +14,27 @@
 //     2^(beta-1), Z = (Z - d_s) / 2^beta for s = S..2, d_1 = Z;
 //   * pairs (s, t) with s + t <= S + 1 are multiplied; pairs of one level
 //     L = s + t accumulate in one FP32 TMEM accumulator, exact because kc
-//     keeps every level sum within 2^24 (BF16: beta 8, kc 128; FP16: beta 9,
+//     keeps every level sum within 2^24 (BF16: beta 8, kc 64; FP16: beta 9,
 //     kc 32);
 //   * per chunk the level sums are combined exactly as a 64-bit integer
 //     I = sum_L P_L 2^(beta (S+1-L)) (|I| < 2^53), turned into the binary64
 //     value I 2^(E_i + F_j - beta (S+1)) without rounding, and added to a
 //     binary64 accumulator that starts from C.
 //
-// Kernel shape: one CTA per 128 x 64 output tile, 128 threads, thread t owns
-// row t of the tile (= TMEM lane t).  Per chunk the threads compute the
-// exponents straight from global memory, then write the digit planes of A
-// (128 x ks) and B (64 x ks) into shared memory in the K-major, no-swizzle
+// Kernel shape: a persistent CTA per SM (512 threads) walks its 128 x 64
+// output tiles and their k-chunks as one pipeline.  Per chunk the threads
+// load A (thread = tile row and a quarter of the chunk) and B into
+// registers, compute the exponents (shared-memory exchange across the four
+// quarters of a row; warp shuffles along B's columns) and write the digit
+// planes into one of two shared-memory stages in the K-major, no-swizzle
 // core-matrix layout (8 rows x 16 bytes per core matrix; LBO 128 bytes
-// between core matrices along k, SBO = ks/8 * 128 bytes between 8-row
+// between core matrices along k, SBO = kc/8 * 128 bytes between 8-row
 // groups); one thread issues tcgen05.mma (M 128, N 64, K 16) for every kept
-// pair and k16 step and commits to an mbarrier.  Waits on that mbarrier are
-// bounded: on expiry the kernel records an error in the plan's status word,
-// releases its TMEM and returns.
+// pair into one of two TMEM accumulator sets and commits to that stage's
+// mbarrier; then the threads recombine the previous chunk from the other
+// set.  Every wait is bounded (2 s): on expiry the kernel records an error in
+// the plan's status word, drains its tensor-core work (bounded), releases
+// its TMEM and returns.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -48,9 +52,9 @@ namespace {
 
 constexpr int kTM = 128;       // tile rows (MMA M)
 constexpr int kTN = 64;        // tile cols (MMA N)
-constexpr int kThreadsS = 128;
-constexpr int kTmemCols = 256; // S levels x 64 columns, rounded to a power of two
-constexpr long long kSpinLimit = 1ll << 26;
+constexpr int kThreadsS = 512;
+constexpr int kTmemCols = 512; // 2 sets x S levels x 64 columns
+constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on any device-side wait
 
 struct SItem {
     int32_t entry, row0, col0, pad;
@@ -59,12 +63,11 @@ struct SItem {
 template <bool FP16, int S>
 struct Cfg {
     static constexpr int beta = FP16 ? 9 : 8;
-    static constexpr int kc = FP16 ? 32 : 128;     // exponent chunk
-    static constexpr int ks = FP16 ? 32 : 64;      // staged sub-chunk
-    static constexpr int planeA = kTM * ks * 2;    // bytes per digit plane of A
-    static constexpr int planeB = kTN * ks * 2;
-    static constexpr int sbo = ks / 8 * 128;
-    static constexpr int smem = S * (planeA + planeB);
+    static constexpr int kc = FP16 ? 32 : 64;      // k-chunk (one exponent per row / column)
+    static constexpr int planeA = kTM * kc * 2;    // bytes per digit plane of A
+    static constexpr int planeB = kTN * kc * 2;
+    static constexpr int sbo = kc / 8 * 128;
+    static constexpr int smem = 2 * S * (planeA + planeB);   // two stages
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -91,8 +94,17 @@ __device__ __forceinline__ uint32_t make_idesc() {
     return d;                                          // A, B K-major; dense
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;\n" : "=l"(t));
+    return t;
+}
+
+// Wait for the mbarrier phase with the given parity; gives up after about
+// kWaitNs nanoseconds of wall time (the caller then reports an error).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (long long i = 0; i < kSpinLimit; ++i) {
+    const unsigned long long t0 = global_ns();
+    for (long long i = 0;; ++i) {
         uint32_t ok;
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
@@ -100,8 +112,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
             : "r"(bar), "r"(parity)
             : "memory");
         if (ok) return true;
+        if ((i & 255) == 255 && global_ns() - t0 > kWaitNs) return false;
     }
-    return false;
 }
 
 // |a| bit pattern (sign cleared) -> E with 2^(E-1) <= |a| < 2^E (a != 0).
@@ -162,27 +174,31 @@ __device__ __forceinline__ double scaled_int_to_double(long long I, int X) {
     return __longlong_as_double((long long)b);
 }
 
+// One CTA per SM, 512 threads, tiles taken round-robin (tile = 128 x 64
+// outputs).  The k-chunks of all of a CTA's tiles form one pipeline: while
+// the tensor cores run chunk i (digit planes and TMEM accumulator set i&1),
+// the threads recombine chunk i-1 from the other TMEM set and then load and
+// slice chunk i+1.  Thread t: row 32 (w % 4) + lane of the tile (w = warp,
+// = its TMEM lane), quarter q = w / 4 of the chunk's columns for slicing and
+// of the tile's 64 output columns for recombination.
 template <bool FP16, int S>
-__global__ void __launch_bounds__(kThreadsS, 2) k_split(const DevDesc* __restrict__ descs,
-                                                         const SItem* __restrict__ items,
-                                                         int* __restrict__ status,
-                                                         float* __restrict__ dump) {
+__global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restrict__ descs,
+                                                         const SItem* __restrict__ items, int n_items,
+                                                         int* __restrict__ status, float* __restrict__ dump) {
     using C_ = Cfg<FP16, S>;
-    constexpr int BETA = C_::beta, KC = C_::kc, KS = C_::ks;
+    constexpr int BETA = C_::beta, KC = C_::kc;
+    constexpr int QC = KC / 4;            // chunk columns of A per thread
+    constexpr int KB = KC / 32;           // k values of B per lane and column
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint8_t* planeA = smem;                                  // S planes of 128 x ks
-    uint8_t* planeB = smem + S * C_::planeA;                 // S planes of 64 x ks
-    __shared__ int s_F[kTN];
-    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ unsigned long long s_rmax[4][kTM];
+    __shared__ int s_E[2][kTM];
+    __shared__ int s_F[2][kTN];
+    __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ uint32_t s_tmem;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const SItem item = items[blockIdx.x];
-    const DevDesc d = descs[item.entry];
-    const int m0 = item.row0, n0 = item.col0;
-    const int row = m0 + tid;
-    const bool row_ok = row < d.m;
-    const int wc = min(kTN, d.n - n0);
+    const int rloc = 32 * (warp & 3) + lane;   // tile row (TMEM lane)
+    const int q = warp >> 2;                   // quarter
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
@@ -190,130 +206,220 @@ __global__ void __launch_bounds__(kThreadsS, 2) k_split(const DevDesc* __restric
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s_bar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s_bar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s_bar[1])));
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = s_tmem;
-    const uint32_t bar = smem_u32(&s_bar);
-    uint32_t phase = 0;
+    const uint32_t idesc = make_idesc<FP16>();
     bool failed = false;
 
-    // binary64 accumulators: row `row`, columns n0 .. n0+63, starting from C
-    double acc[kTN];
-#pragma unroll
-    for (int j = 0; j < kTN; ++j) acc[j] = 0.0;
-    if (row_ok) {
-#pragma unroll
-        for (int j = 0; j < kTN; ++j)
-            if (j < wc) acc[j] = d.C[(size_t)row + (size_t)(n0 + j) * (size_t)d.ldc];
-    }
+    // the chunk whose MMAs are in flight (recombined one iteration later)
+    struct Prev {
+        DevDesc d;
+        int row0, col0, c, stage;
+        bool last;
+    } prev{};
+    bool have_prev = false;
+    double acc[16];
 
-    const uint32_t idesc = make_idesc<FP16>();
-    const int nchunks = (d.k + KC - 1) / KC;
-    for (int c = 0; c < nchunks; ++c) {
-        const int k0 = c * KC;
-        const int kcl = min(KC, d.k - k0);
-        // ---- exponents: row of A (this thread), columns of B (warp-wide) ----
-        int E = 0;
-        if (row_ok) {
-            unsigned long long mx = 0;
-            const double* a = d.A + (size_t)row + (size_t)k0 * (size_t)d.lda;
-#pragma unroll 8
-            for (int p = 0; p < kcl; ++p) {
-                const unsigned long long v =
-                    (unsigned long long)__double_as_longlong(__ldg(a + (size_t)p * (size_t)d.lda)) & 0x7FFFFFFFFFFFFFFFull;
-                mx = v > mx ? v : mx;
-            }
-            E = mx ? exp_of_bits(mx) : 0;
+    auto load_c0 = [&](const DevDesc& d, int row0, int col0) {
+        const int row = row0 + rloc;
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+            const int col = col0 + 16 * q + jj;
+            acc[jj] = (row < d.m && col < d.n) ? d.C[(size_t)row + (size_t)col * (size_t)d.ldc] : 0.0;
         }
-        for (int j = warp; j < kTN; j += kThreadsS / 32) {
-            unsigned long long mx = 0;
-            if (j < wc) {
-                const double* b = d.B + (size_t)k0 + (size_t)(n0 + j) * (size_t)d.ldb;
-                for (int p = lane; p < kcl; p += 32) {
-                    const unsigned long long v =
-                        (unsigned long long)__double_as_longlong(__ldg(b + p)) & 0x7FFFFFFFFFFFFFFFull;
+    };
+
+    // recombine `prev` into acc (its MMAs committed to s_bar[prev.stage])
+    auto recombine = [&](uint32_t parity) -> bool {
+        // warp-uniform decision before the warp-collective TMEM loads
+        if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&s_bar[prev.stage]), parity))) return false;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        uint32_t v[S][16];
+        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+#pragma unroll
+        for (int l = 0; l < S; ++l) {
+            const uint32_t ta = tmem + lane_base + (uint32_t)(prev.stage * S * kTN + l * kTN + 16 * q);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];\n"
+                : "=r"(v[l][0]), "=r"(v[l][1]), "=r"(v[l][2]), "=r"(v[l][3]), "=r"(v[l][4]), "=r"(v[l][5]),
+                  "=r"(v[l][6]), "=r"(v[l][7]), "=r"(v[l][8]), "=r"(v[l][9]), "=r"(v[l][10]), "=r"(v[l][11]),
+                  "=r"(v[l][12]), "=r"(v[l][13]), "=r"(v[l][14]), "=r"(v[l][15])
+                : "r"(ta));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        const int E = s_E[prev.stage][rloc];
+        const int row = prev.row0 + rloc;
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+            const int j = 16 * q + jj;
+            long long I = 0;
+#pragma unroll
+            for (int l = 0; l < S; ++l)   // level L = l + 2, weight 2^(beta (S - 1 - l))
+                I = (I << BETA) + (long long)__float2int_rn(__uint_as_float(v[l][jj]));
+            if (dump != nullptr && row < prev.d.m && prev.col0 + j < prev.d.n) {
+#pragma unroll
+                for (int l = 0; l < S; ++l)
+                    dump[(((size_t)prev.c * S + l) * prev.d.m + row) * prev.d.n + (prev.col0 + j)] =
+                        __uint_as_float(v[l][jj]);
+            }
+            acc[jj] += scaled_int_to_double(I, E + s_F[prev.stage][j] - BETA * (S + 1));
+        }
+        return true;
+    };
+
+    auto store_prev = [&]() {
+        const int row = prev.row0 + rloc;
+        if (row < prev.d.m) {
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+                const int col = prev.col0 + 16 * q + jj;
+                if (col < prev.d.n) prev.d.C[(size_t)row + (size_t)col * (size_t)prev.d.ldc] = acc[jj];
+            }
+        }
+    };
+
+    int iter = 0;
+    int last_commit = -1;     // iteration of the most recent tensor-core commit
+    int t = blockIdx.x;
+    if (t < n_items) {
+        const SItem it0 = items[t];
+        load_c0(descs[it0.entry], it0.row0, it0.col0);
+    }
+    while (t < n_items) {
+        const SItem item = items[t];
+        const DevDesc d = descs[item.entry];
+        const int m0 = item.row0, n0 = item.col0;
+        const int nch = (d.k + KC - 1) / KC;
+        const int row = m0 + rloc;
+        const bool row_ok = row < d.m;
+        const int wc = min(kTN, d.n - n0);
+        for (int c = 0; c < nch; ++c, ++iter) {
+            const int stage = iter & 1;
+            const int k0 = c * KC;
+            const int kcl = min(KC, d.k - k0);
+            uint8_t* planeA = smem + stage * (S * (C_::planeA + C_::planeB));
+            uint8_t* planeB = planeA + S * C_::planeA;
+            // (1) loads: A row `row`, chunk columns [q QC, q QC + QC); B columns 4 w .. 4 w + 3
+            double av[QC];
+#pragma unroll
+            for (int p = 0; p < QC; ++p) {
+                const int col = q * QC + p;
+                av[p] = (row_ok && col < kcl) ? __ldg(d.A + (size_t)row + (size_t)(k0 + col) * (size_t)d.lda) : 0.0;
+            }
+            double bv[4][KB];
+#pragma unroll
+            for (int jc = 0; jc < 4; ++jc) {
+                const int j = 4 * warp + jc;
+#pragma unroll
+                for (int h = 0; h < KB; ++h) {
+                    const int kk = lane + 32 * h;
+                    bv[jc][h] = (j < wc && kk < kcl) ? __ldg(d.B + (size_t)(k0 + kk) + (size_t)(n0 + j) * (size_t)d.ldb)
+                                                     : 0.0;
+                }
+            }
+            // (2) exponents
+            {
+                unsigned long long mx = 0;
+#pragma unroll
+                for (int p = 0; p < QC; ++p) {
+                    const unsigned long long v = (unsigned long long)__double_as_longlong(av[p]) & 0x7FFFFFFFFFFFFFFFull;
                     mx = v > mx ? v : mx;
                 }
+                s_rmax[q][rloc] = mx;
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long w = __shfl_xor_sync(0xffffffffu, mx, o);
-                mx = w > mx ? w : mx;
+            for (int jc = 0; jc < 4; ++jc) {
+                unsigned long long mx = 0;
+#pragma unroll
+                for (int h = 0; h < KB; ++h) {
+                    const unsigned long long v =
+                        (unsigned long long)__double_as_longlong(bv[jc][h]) & 0x7FFFFFFFFFFFFFFFull;
+                    mx = v > mx ? v : mx;
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long w = __shfl_xor_sync(0xffffffffu, mx, o);
+                    mx = w > mx ? w : mx;
+                }
+                if (lane == 0) s_F[stage][4 * warp + jc] = mx ? exp_of_bits(mx) : 0;
             }
-            if (lane == 0) s_F[j] = mx ? exp_of_bits(mx) : 0;
-        }
-        __syncthreads();
-
-        // ---- sub-chunks: digits to shared memory, then the tensor-core pass ----
-        for (int h0 = 0; h0 < KC; h0 += KS) {
-            const int kb = k0 + h0;                // first k of this sub-chunk
-            if (kb >= d.k) break;                  // ragged last chunk
-            const int kl = max(0, min(KS, d.k - kb));
-            // A digits: this thread's row, KS columns, 8 at a time (16-byte stores)
+            __syncthreads();
+            int E;
             {
-                const double* a = d.A + (size_t)row + (size_t)kb * (size_t)d.lda;
-                uint8_t* dst = planeA + (tid >> 3) * C_::sbo + (tid & 7) * 16;
-#pragma unroll 1
-                for (int g = 0; g < KS / 8; ++g) {
+                unsigned long long mx = s_rmax[0][rloc];
+#pragma unroll
+                for (int qq = 1; qq < 4; ++qq) mx = s_rmax[qq][rloc] > mx ? s_rmax[qq][rloc] : mx;
+                E = mx ? exp_of_bits(mx) : 0;
+                if (q == 0) s_E[stage][rloc] = E;
+            }
+            // (3) digits into the planes of this stage (free: their MMAs were
+            // waited for when the previous chunk was recombined)
+            {
+                uint8_t* dst = planeA + (rloc >> 3) * C_::sbo + (rloc & 7) * 16 + (q * QC / 8) * 128;
+#pragma unroll
+                for (int g = 0; g < QC / 8; ++g) {
                     uint32_t packed[S][4];
 #pragma unroll
-                    for (int q = 0; q < 8; q += 2) {
-                        int dg0[S], dg1[S];
-                        const int kk = g * 8 + q;
-                        const double a0 = (row_ok && kk < kl) ? __ldg(a + (size_t)kk * (size_t)d.lda) : 0.0;
-                        const double a1 = (row_ok && kk + 1 < kl) ? __ldg(a + (size_t)(kk + 1) * (size_t)d.lda) : 0.0;
-                        make_digits<S, BETA>(a0, E, dg0);
-                        make_digits<S, BETA>(a1, E, dg1);
+                    for (int p = 0; p < 8; p += 2) {
+                        int d0[S], d1[S];
+                        make_digits<S, BETA>(av[8 * g + p], E, d0);
+                        make_digits<S, BETA>(av[8 * g + p + 1], E, d1);
 #pragma unroll
-                        for (int s = 0; s < S; ++s)
-                            packed[s][q >> 1] = (uint32_t)digit_bits<FP16>(dg0[s]) |
-                                                ((uint32_t)digit_bits<FP16>(dg1[s]) << 16);
+                        for (int s2 = 0; s2 < S; ++s2)
+                            packed[s2][p >> 1] =
+                                (uint32_t)digit_bits<FP16>(d0[s2]) | ((uint32_t)digit_bits<FP16>(d1[s2]) << 16);
                     }
 #pragma unroll
-                    for (int s = 0; s < S; ++s)
-                        *reinterpret_cast<uint4*>(dst + s * C_::planeA + g * 128) =
-                            make_uint4(packed[s][0], packed[s][1], packed[s][2], packed[s][3]);
+                    for (int s2 = 0; s2 < S; ++s2)
+                        *reinterpret_cast<uint4*>(dst + s2 * C_::planeA + g * 128) =
+                            make_uint4(packed[s2][0], packed[s2][1], packed[s2][2], packed[s2][3]);
                 }
             }
-            // B digits: warp w takes columns w, w+4, ...; lanes run along k
-            for (int j = warp; j < kTN; j += kThreadsS / 32) {
-                const int F = s_F[j];
-                const double* b = d.B + (size_t)kb + (size_t)(n0 + j) * (size_t)d.ldb;
-                uint8_t* dst = planeB + (j >> 3) * C_::sbo + (j & 7) * 16;
-                for (int kk = lane; kk < KS; kk += 32) {
-                    const double bv = (j < wc && kk < kl) ? __ldg(b + kk) : 0.0;
-                    int dg[S];
-                    make_digits<S, BETA>(bv, F, dg);
 #pragma unroll
-                    for (int s = 0; s < S; ++s)
-                        *reinterpret_cast<uint16_t*>(dst + s * C_::planeB + (kk >> 3) * 128 + (kk & 7) * 2) =
-                            digit_bits<FP16>(dg[s]);
+            for (int jc = 0; jc < 4; ++jc) {
+                const int j = 4 * warp + jc;
+                const int F = s_F[stage][j];
+                uint8_t* dst = planeB + (j >> 3) * C_::sbo + (j & 7) * 16;
+#pragma unroll
+                for (int h = 0; h < KB; ++h) {
+                    const int kk = lane + 32 * h;
+                    int dg[S];
+                    make_digits<S, BETA>(bv[jc][h], F, dg);
+#pragma unroll
+                    for (int s2 = 0; s2 < S; ++s2)
+                        *reinterpret_cast<uint16_t*>(dst + s2 * C_::planeB + (kk >> 3) * 128 + (kk & 7) * 2) =
+                            digit_bits<FP16>(dg[s2]);
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             __syncthreads();
+            // (4) one thread issues the chunk's tensor-core work
             if (tid == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 bool first_of_level[S + 2];
 #pragma unroll
-                for (int L = 0; L < S + 2; ++L) first_of_level[L] = (h0 == 0);
+                for (int L = 0; L < S + 2; ++L) first_of_level[L] = true;
 #pragma unroll
-                for (int s = 1; s <= S; ++s) {
+                for (int s1 = 1; s1 <= S; ++s1) {
 #pragma unroll
-                    for (int t = 1; t <= S; ++t) {
-                        if (s + t > S + 1) continue;
-                        const int L = s + t;
-                        const uint32_t dcol = tmem + (uint32_t)((L - 2) * kTN);
-                        const uint32_t a_base = smem_u32(planeA + (s - 1) * C_::planeA);
-                        const uint32_t b_base = smem_u32(planeB + (t - 1) * C_::planeB);
+                    for (int t1 = 1; t1 <= S; ++t1) {
+                        if (s1 + t1 > S + 1) continue;
+                        const int L = s1 + t1;
+                        const uint32_t dcol = tmem + (uint32_t)(stage * S * kTN + (L - 2) * kTN);
+                        const uint32_t a_base = smem_u32(planeA + (s1 - 1) * C_::planeA);
+                        const uint32_t b_base = smem_u32(planeB + (t1 - 1) * C_::planeB);
 #pragma unroll
-                        for (int q = 0; q < KS / 16; ++q) {
-                            const uint64_t ad = make_desc(a_base + q * 256, C_::sbo);
-                            const uint64_t bd = make_desc(b_base + q * 256, C_::sbo);
+                        for (int kq = 0; kq < KC / 16; ++kq) {
+                            const uint64_t ad = make_desc(a_base + kq * 256, C_::sbo);
+                            const uint64_t bd = make_desc(b_base + kq * 256, C_::sbo);
                             const uint32_t accum = first_of_level[L] ? 0u : 1u;
                             first_of_level[L] = false;
                             asm volatile(
@@ -323,69 +429,44 @@ __global__ void __launch_bounds__(kThreadsS, 2) k_split(const DevDesc* __restric
                         }
                     }
                 }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                                 smem_u32(&s_bar[stage]))
                              : "memory");
             }
-            // the digit planes are reused by the next sub-chunk: wait for the MMAs
-            if (!mbar_wait(bar, phase)) failed = true;
-            phase ^= 1;
-            if (__syncthreads_or(failed)) break;
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        }
-        if (__syncthreads_or(failed)) {
-            failed = true;
-            break;
-        }
-
-        // ---- recombination of this chunk: TMEM levels -> exact binary64 ----
-        {
-            const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-#pragma unroll
-            for (int g = 0; g < kTN / 16; ++g) {
-                uint32_t v[S][16];
-#pragma unroll
-                for (int l = 0; l < S; ++l) {
-                    const uint32_t ta = tmem + lane_base + (uint32_t)(l * kTN + g * 16);
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                        "[%16];\n"
-                        : "=r"(v[l][0]), "=r"(v[l][1]), "=r"(v[l][2]), "=r"(v[l][3]), "=r"(v[l][4]), "=r"(v[l][5]),
-                          "=r"(v[l][6]), "=r"(v[l][7]), "=r"(v[l][8]), "=r"(v[l][9]), "=r"(v[l][10]), "=r"(v[l][11]),
-                          "=r"(v[l][12]), "=r"(v[l][13]), "=r"(v[l][14]), "=r"(v[l][15])
-                        : "r"(ta));
+            last_commit = iter;
+            // (5) recombine the previous chunk while this one runs
+            if (have_prev) {
+                const bool ok = recombine((uint32_t)(((iter - 1) >> 1) & 1));
+                if (__syncthreads_or(!ok)) {
+                    failed = true;
+                    break;
                 }
-                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-                for (int jj = 0; jj < 16; ++jj) {
-                    const int j = g * 16 + jj;
-                    long long I = 0;
-#pragma unroll
-                    for (int l = 0; l < S; ++l)   // level L = l + 2, weight 2^(beta (S - 1 - l))
-                        I = (I << BETA) + (long long)__float2int_rn(__uint_as_float(v[l][jj]));
-                    if (dump != nullptr && row_ok && j < wc) {
-                        // exactness probe: the raw FP32 level sums of chunk c
-#pragma unroll
-                        for (int l = 0; l < S; ++l)
-                            dump[(((size_t)c * S + l) * d.m + row) * d.n + (n0 + j)] = __uint_as_float(v[l][jj]);
-                    }
-                    acc[j] += scaled_int_to_double(I, E + s_F[j] - BETA * (S + 1));
+                if (prev.last) {
+                    store_prev();
+                    load_c0(d, m0, n0);   // chunk c is chunk 0 of this tile; consumed next iteration
                 }
             }
-            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            prev.d = d;
+            prev.row0 = m0;
+            prev.col0 = n0;
+            prev.c = c;
+            prev.stage = stage;
+            prev.last = (c == nch - 1);
+            have_prev = true;
         }
-        __syncthreads();   // TMEM reads and s_F use are done before the next chunk
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        if (failed) break;
+        t += gridDim.x;
     }
-
-    if (row_ok && !failed) {
-#pragma unroll
-        for (int j = 0; j < kTN; ++j)
-            if (j < wc) d.C[(size_t)row + (size_t)(n0 + j) * (size_t)d.ldc] = acc[j];
+    if (have_prev && !failed) {
+        const bool ok = recombine((uint32_t)(((iter - 1) >> 1) & 1));
+        if (__syncthreads_or(!ok)) failed = true;
+        if (!failed) store_prev();
     }
     if (failed) {
         // a wait expired: give the tensor-core work in flight one more bounded
         // wait before the TMEM it writes is released, and report the failure
-        mbar_wait(bar, phase ^ 1);
+        if (last_commit >= 0)
+            mbar_wait(smem_u32(&s_bar[last_commit & 1]), (uint32_t)((last_commit >> 1) & 1));
         if (tid == 0) atomicExch(status, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -400,7 +481,11 @@ cudaError_t launch_t(const DevDesc* descs, const SItem* items, int n_items, int*
     cudaError_t e = cudaFuncSetAttribute(k_split<FP16, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     if (n_items <= 0) return cudaSuccess;
-    k_split<FP16, S><<<n_items, kThreadsS, smem, s>>>(descs, items, status, dump);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::max(1, std::min(n_items, sms));
+    k_split<FP16, S><<<grid, kThreadsS, smem, s>>>(descs, items, n_items, status, dump);
     return cudaGetLastError();
 }
 
@@ -427,7 +512,7 @@ struct SplitPlan {
 };
 
 int chunk_len(int precision) {
-    return (precision == LRB_PREC_SPLIT_FP16_S3 || precision == LRB_PREC_SPLIT_FP16_S4) ? 32 : 128;
+    return (precision == LRB_PREC_SPLIT_FP16_S3 || precision == LRB_PREC_SPLIT_FP16_S4) ? 32 : 64;
 }
 int digit_count(int precision) {
     return (precision == LRB_PREC_SPLIT_BF16_S3 || precision == LRB_PREC_SPLIT_FP16_S3) ? 3 : 4;
@@ -472,7 +557,10 @@ lrb_status create(int device, int sms, const lrb_gemm_desc* descs, size_t count,
     }
     info->items = p->n_items;
     info->groups = 1;
-    info->grid = p->n_items;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    info->grid = std::max(1, std::min(p->n_items, nsm));
     *out = p;
     return LRB_OK;
 }

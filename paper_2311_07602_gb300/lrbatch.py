@@ -43,7 +43,15 @@ class lrb_plan_opts(ctypes.Structure):
 class lrb_plan_info(ctypes.Structure):
     _fields_ = [("entries", ctypes.c_int64), ("items", ctypes.c_int64), ("groups", ctypes.c_int64),
                 ("flops", ctypes.c_double), ("alg_bytes", ctypes.c_double), ("grid", ctypes.c_int32),
-                ("precision", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("dmma_items", ctypes.c_int64)]
+
+
+class lrb_queue_stats_t(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("accepted", "rejected_budget", "rejected_full", "rejected_invalid",
+                                               "completed", "failed", "waiting", "waves", "max_concurrent_waves")] + \
+               [("mean_wave_entries", ctypes.c_double)] + \
+               [(n, ctypes.c_uint64) for n in ("reserved_bytes", "peak_reserved_bytes", "budget_bytes")] + \
+               [(n, ctypes.c_double) for n in ("p50_ms", "p99_ms", "mean_ms", "max_ms", "gflops", "flops_done")]
 
 
 class LrbError(RuntimeError):
@@ -75,6 +83,14 @@ def lib():
             "lrb_execute_host": ([vp, vp, sz, ctypes.POINTER(lrb_plan_opts), vp], i32),
             "lrb_launch_noalloc": ([vp, sz, vp], i32),
             "lrb_plan_status": ([vp], i32),
+            "lrb_queue_create": ([vp, sz, ctypes.c_int, ctypes.POINTER(vp)], i32),
+            "lrb_queue_set_limits": ([vp, sz, sz], i32),
+            "lrb_queue_submit": ([vp, vp, sz, ctypes.POINTER(ctypes.c_uint64)], i32),
+            "lrb_queue_poll": ([vp, ctypes.c_uint64], i32),
+            "lrb_queue_wait": ([vp, ctypes.c_uint64, ctypes.c_int], i32),
+            "lrb_queue_latency": ([vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)], i32),
+            "lrb_queue_stats": ([vp, ctypes.POINTER(lrb_queue_stats_t)], i32),
+            "lrb_queue_destroy": ([vp, ctypes.c_int], i32),
             "lrb_split_dump_levels": ([vp, vp, vp], i32),
             "lrb_plan_tiles_host": ([vp, sz, i32, vp, sz, ctypes.POINTER(sz)], i32),
             "lrb_variant_count": ([], i32),
@@ -237,6 +253,53 @@ class Plan:
         if self.ptr:
             check(lib().lrb_plan_destroy(self.ptr))
             self.ptr = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Queue:
+    """lrb_queue_*: continuous-batching request queue on one handle."""
+
+    def __init__(self, handle: Handle, budget_bytes: int, max_inflight: int = 4):
+        self.ptr = ctypes.c_void_p()
+        check(lib().lrb_queue_create(handle.ptr, int(budget_bytes), max_inflight, ctypes.byref(self.ptr)))
+
+    def set_limits(self, max_waiting: int, max_wave_entries: int = 1 << 16):
+        check(lib().lrb_queue_set_limits(self.ptr, max_waiting, max_wave_entries))
+
+    def submit(self, descs: np.ndarray):
+        """Returns (status, ticket); status is LRB_OK, LRB_ERR_BUDGET, LRB_ERR_QUEUE_FULL or LRB_ERR_INVALID."""
+        d = np.ascontiguousarray(descs, dtype=DESC_DTYPE)
+        t = ctypes.c_uint64(0)
+        st = lib().lrb_queue_submit(self.ptr, d.ctypes.data if len(d) else None, len(d), ctypes.byref(t))
+        return st, t.value
+
+    def poll(self, ticket: int) -> int:
+        return lib().lrb_queue_poll(self.ptr, ticket)
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> int:
+        return lib().lrb_queue_wait(self.ptr, ticket, timeout_ms)
+
+    def latency(self, ticket: int) -> float:
+        v = ctypes.c_double(0)
+        check(lib().lrb_queue_latency(self.ptr, ticket, ctypes.byref(v)))
+        return v.value
+
+    def stats(self) -> dict:
+        s = lrb_queue_stats_t()
+        check(lib().lrb_queue_stats(self.ptr, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in lrb_queue_stats_t._fields_}
+
+    def close(self, timeout_ms: int = -1) -> int:
+        st = LRB_OK
+        if self.ptr:
+            st = lib().lrb_queue_destroy(self.ptr, timeout_ms)
+            self.ptr = ctypes.c_void_p()
+        return st
 
     def __enter__(self):
         return self

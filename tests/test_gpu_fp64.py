@@ -204,3 +204,45 @@ def test_variable_size_full_size_sampled(handle):
     sample_check(b, b.C, c0, s)
     del b
     torch.cuda.empty_cache()
+
+
+def test_execute_host_pipelined_pieces(handle):
+    """lrb_execute_host on host buffers: ~200 MB of pinned entries (several
+    pipelined pieces, run twice so the cached plans are reused) and pageable
+    entries with padded leading dimensions (2-D copies) where two entries
+    share one A (copied once); every C against the oracle, padding untouched."""
+    big = W.uniform_batch(W.FORM_O, 512, 16, 96, dist="normal", seed=61)          # 96 x 2 MB of C
+    Ah, Bh, C0 = host(big.A), host(big.B), host(big.C)
+    pinned = [torch.from_numpy(x.copy()).pin_memory() for x in (Ah, Bh, C0)]
+    small = ragged_batch([(100, 30, 40), (37, 5, 19), (100, 30, 40)], pad=3, seed=62)
+    sA, sB, sC0 = host(small.A), host(small.B), host(small.C)
+    sC = sC0.copy()
+
+    def rows(ptrs, b):
+        d = np.zeros(len(b), dtype=L.DESC_DTYPE)
+        for key, base, off in (("A", ptrs[0], b.offA), ("B", ptrs[1], b.offB), ("C", ptrs[2], b.offC)):
+            d[key] = np.uint64(base) + 8 * off.astype(np.uint64)
+        for key in ("m", "n", "k", "lda", "ldb", "ldc"):
+            d[key] = getattr(b, key)
+        return d
+
+    d_big = rows([t.data_ptr() for t in pinned], big)
+    d_small = rows([sA.ctypes.data, sB.ctypes.data, sC.ctypes.data], small)
+    d_small["A"][2] = d_small["A"][0]              # entry 2 shares entry 0's A
+    small_shared = W.Batch(small.A, small.B, small.C, small.m, small.n, small.k, small.lda, small.ldb, small.ldc,
+                           np.array([small.offA[0], small.offA[1], small.offA[0]]), small.offB, small.offC)
+
+    handle.execute_host(np.concatenate([d_big, d_small]))
+    exp1 = oracle_batch(Ah, Bh, C0, big)
+    check_entries(pinned[2].numpy().copy(), exp1, Ah, Bh, C0, big)
+    exp_s = oracle_batch(sA, sB, sC0, small_shared)
+    check_entries(sC.copy(), exp_s, sA, sB, sC0, small_shared)
+    written = np.zeros(len(sC), dtype=bool)
+    for e in range(len(small)):
+        entry_view(written, int(small.offC[e]), int(small.m[e]), int(small.n[e]), int(small.ldc[e]))[...] = True
+    assert np.array_equal(sC[~written].view(np.uint64), sC0[~written].view(np.uint64))
+
+    handle.execute_host(d_big)                     # second call on the big part alone
+    handle.execute_host(d_big)                     # and again: cached plans
+    exp3 = oracle_batch(Ah, Bh, oracle_batch(Ah, Bh, exp1, big), big)
+    check_entries(pinned[2].numpy().copy(), exp3, Ah, Bh, exp1, big, tol=3e-13)
