@@ -182,9 +182,10 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other workloads (64-entry O-form, variable-size, split precision, serving)")
-    ap.add_argument("--extras", default="small,variable,split,serving,dmma",
+    ap.add_argument("--extras", default="small,variable,split,serving,dmma,lr",
                     help="comma-separated subset of the other workloads to run")
     ap.add_argument("--split-batch", type=int, default=2048, help="entries of the split-precision batch")
+    ap.add_argument("--dmma-scale", type=float, default=0.25, help="batch-count scale of the DMMA comparison")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="batch-count scale of every group (profiling runs use a small case)")
     args = ap.parse_args()
@@ -300,7 +301,8 @@ def main():
         plan = None
         del batches
         torch.cuda.empty_cache()
-        line["extras"] = extras(L, handle, stream, dev, peak, timed, set(args.extras.split(",")), args.split_batch)
+        line["extras"] = extras(L, handle, stream, dev, peak, timed, set(args.extras.split(",")), args.split_batch,
+                                args.dmma_scale)
 
     if not args.no_cpu and rank == 0 and world == 1:
         f, s, used, ents = cpu_baseline(args.cpu_fraction)
@@ -317,7 +319,7 @@ def main():
     return 0
 
 
-def extras(L, handle, stream, dev, peak_fp64, timed, which, split_batch):
+def extras(L, handle, stream, dev, peak_fp64, timed, which, split_batch, dmma_scale=0.25):
     """The other workloads, each with its own plan, 3 warm-up and 5 timed launches:
     the 64-entry O-form batch (L2 flushed before every launch: it fits in L2),
     the 20,000-entry variable-size batch (persistent vs one launch per shape),
@@ -341,8 +343,58 @@ def extras(L, handle, stream, dev, peak_fp64, timed, which, split_batch):
     if "serving" in which:
         out["serving"] = serving_leg(L, handle, dev, peak_fp64)
     if "dmma" in which:
-        out["dmma"] = dmma_leg(L, handle, dev, peak_fp64, timed)
+        out["dmma"] = dmma_leg(L, handle, dev, peak_fp64, timed, dmma_scale)
+    if "lr" in which:
+        out["lr_chain"] = lr_leg(L, handle, dev, peak_fp64, timed)
     return out
+
+
+# GFLOPS the paper prints for its fused batched low-rank multiplication and
+# the vendor libraries, batch 20,000 (context only: CPUs, other hardware).
+PAPER_LR_GFLOPS = {
+    "rank 96, 48-core A64FX (ours / SSL-2)": {512: (207.55, 370.62), 1024: (343.912, 598.93), 2048: (521.93, 851.74)},
+    "rank 128, 2x Xeon 6148 40 cores (ours / MKL BATCH)": {512: (339.849, 262.281), 1024: (361.89, 400.602),
+                                                           2048: (319.161, 554.721)},
+    "rank 96, 2x EPYC 7502 64 cores (ours / BLIS)": {512: (237.441, 197.056), 1024: (283.175, 373.555),
+                                                     2048: (348.566, 559.075)},
+}
+
+
+def lr_leg(L, handle, dev, peak_fp64, timed, batch=20000):
+    """The paper's batched low-rank multiplication G = A_X (A_{V^T} B_U) B_X
+    (Alg. 1-3): batch 20,000, b in {512, 1024, 2048}, r in {8, 16, 32}, N(0,1),
+    fused (one CTA per block, temporaries on chip) against unfused (three
+    batched products through the persistent FP64 path).  GFLOPS counted as the
+    paper does, batch (4 r^3 + 2 r^2 b) / t; bandwidth as batch (2 r^2 + 2 r b)
+    8 bytes / t.  Ranks 96 and 128 (the paper's tables) run unfused."""
+    import torch
+    from paper_2311_07602_gb300 import workloads as W
+    rows = []
+    for r in (8, 16, 32, 96, 128):
+        for b in (512, 1024, 2048):
+            lb = W.lr_batch(batch, b, r, seed=7000 + 10 * r + b // 512, device=dev)
+            d = L.lr_descs_for(lb)
+            fpap = lb.flops_paper()
+            byts = batch * (2 * r * r + 2 * r * b) * 8.0
+            row = {"r": r, "b": b}
+            for fused in ((True, False) if r <= 64 else (False,)):
+                with L.Plan(handle, d, lr_fused=fused) as p:
+                    steps = 3 if r <= 64 else 1
+                    ms, _ = timed(lambda s: p.launch(s), steps, 3)
+                    ms /= steps
+                    exec_flops = p.info()["flops"]
+                key = "fused" if fused else "unfused"
+                row[key] = {"ms": round(ms, 3), "gflops_paper_count": round(fpap / ms / 1e6, 1),
+                            "gib_s": round(byts / (ms / 1e3) / 2 ** 30, 1),
+                            "frac_fp64_peak": round(exec_flops / ms / 1e9 / peak_fp64, 4)}
+            if "fused" in row:
+                row["fused_vs_unfused"] = round(row["unfused"]["ms"] / row["fused"]["ms"], 3)
+            rows.append(row)
+            del lb
+            torch.cuda.empty_cache()
+    return {"workload": f"batch {batch}, N(0,1), FP64; flops counted as the paper does (4 r^3 + 2 r^2 b per block)",
+            "rows": rows, "paper_cpu_gflops_context": {k: {str(b): v for b, v in t.items()}
+                                                       for k, t in PAPER_LR_GFLOPS.items()}}
 
 
 def dmma_leg(L, handle, dev, peak_fp64, timed, scale=0.25):

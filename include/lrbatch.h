@@ -80,7 +80,10 @@ typedef struct lrb_plan_opts {
     int32_t tune;           /* 1: time candidate tiles for unseen shape buckets; 0: heuristic */
     int32_t force_variant;  /* >= 0: use this FP64 tile variant for every entry (testing) */
     int32_t check_alias;    /* 1: reject overlapping C ranges (LRB_ERR_ALIAS) */
-    int32_t reserved[3];
+    int32_t test_stall;     /* testing only, split plans: the kernel waits once on a barrier nothing
+                               arrives on, so its bounded wait expires and lrb_plan_status reports
+                               LRB_ERR_TIMEOUT (exercises the failure path without a GPU fault) */
+    int32_t reserved[2];
 } lrb_plan_opts;
 
 typedef struct lrb_handle lrb_handle;
@@ -177,6 +180,34 @@ lrb_status lrb_plan_tiles_host(const lrb_gemm_desc* host_descs, size_t count, in
 /* Number of FP64 tile variants and their tile extents (rows x cols). */
 int32_t lrb_variant_count(void);
 lrb_status lrb_variant_shape(int32_t variant, int32_t* bm, int32_t* bn, int32_t* is_dmma);
+
+/* ---- the low-rank multiplication core (Alg. 1, batched as in Alg. 2) -------
+ * For low-rank blocks A = A_U A_X A_{V^T} (rank ra, Eq. 1) and
+ * B = B_U B_X B_{V^T} (rank rb) the product is A_U G B_{V^T} with
+ *     G = A_X (A_{V^T} B_U) B_X          (ra x rb; A_{V^T}: ra x k, B_U: k x rb)
+ * which the paper computes for a batch of independent blocks.  One entry:
+ * device pointers, column-major, leading dimensions >= rows; G is WRITTEN
+ * (Alg. 1 assigns G_XY), not accumulated; G must not overlap the operands. */
+typedef struct lrb_lr_desc {
+    const double* AVT;
+    const double* BU;
+    const double* AX;
+    const double* BX;
+    double* G;
+    int32_t ra, rb, k;
+    int32_t ld_avt, ld_bu, ld_ax, ld_bx, ldg;
+} lrb_lr_desc;
+
+/* Plans a batch of chains (host descriptor array, copied).  fused = 1: one
+ * CTA per block keeps C_temp and E_temp on chip (ranks 1..64, else
+ * LRB_ERR_UNSUPPORTED).  fused = 0: the comparator -- three batched
+ * multiplications C_temp = A_{V^T} B_U, E_temp = A_X C_temp, G = E_temp B_X
+ * through the persistent FP64 path, with temporaries in plan-owned device
+ * memory (any ranks).  lrb_launch runs it; lrb_plan_get_info reports the
+ * chain's flops (ra rb (2k + 2ra + 2rb) per block; the paper counts
+ * 4r^3 + 2r^2 k for ra = rb = r) and bytes. */
+lrb_status lrb_lr_plan_create(lrb_handle* h, const lrb_lr_desc* host_descs, size_t count, int32_t fused,
+                              lrb_plan** out);
 
 /* ---- launch without device allocation -----------------------------------
  * The paper has no counterpart: this serves callers that cannot call

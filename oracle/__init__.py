@@ -45,6 +45,10 @@ def lib():
         L.oracle_gemm_elements.restype = None
         L.oracle_gemm_absbound.argtypes = [i32, i32, i32, _dp, i32, _dp, i32, _dp, i32, _dp]
         L.oracle_gemm_absbound.restype = None
+        L.oracle_lr_chain.argtypes = [i32, i32, i32, _dp, i32, _dp, i32, _dp, i32, _dp, i32, _dp, i32, _dp]
+        L.oracle_lr_chain.restype = None
+        L.oracle_lr_chain_batch.argtypes = [i64] + [ctypes.c_void_p] * 8 + [ctypes.c_int]
+        L.oracle_lr_chain_batch.restype = ctypes.c_int
         L.oracle_max_threads.argtypes = []
         L.oracle_max_threads.restype = ctypes.c_int
         _lib = L
@@ -108,6 +112,36 @@ def absbound(m, n, k, A, offA, lda, B, offB, ldb, C0, offC, ldc) -> np.ndarray:
     lib().oracle_gemm_absbound(m, n, k, _ptr(A, offA), lda, _ptr(B, offB), ldb,
                                _ptr(C0, offC), ldc, _ptr(out))
     return out.reshape(n, m).T
+
+
+def lr_chain(AVT: np.ndarray, BU: np.ndarray, AX: np.ndarray, BX: np.ndarray) -> np.ndarray:
+    """G = A_X (A_{V^T} B_U) B_X for one entry (Alg. 1); 2-D float64 arrays,
+    any memory order; returns G (ra x rb)."""
+    ra, k = AVT.shape
+    rb = BU.shape[1]
+    f = lambda x: np.ascontiguousarray(np.asarray(x, dtype=np.float64).ravel(order="F"))
+    a, b, x, y = f(AVT), f(BU), f(AX), f(BX)
+    G = np.zeros(ra * rb)
+    work = np.zeros(2 * ra * rb)
+    lib().oracle_lr_chain(ra, rb, k, _ptr(a), ra, _ptr(b), k, _ptr(x), ra, _ptr(y), rb, _ptr(G), ra, _ptr(work))
+    return G.reshape(rb, ra).T
+
+
+def lr_chain_batch(bufs: dict, offs: dict, ra, rb, k, nthreads: int = 0) -> int:
+    """Chains on flat buffers: bufs/offs keyed AVT, BU, AX, BX, G (tight
+    leading dimensions); per-entry arrays ra, rb, k.  Writes G in place."""
+    cnt = len(ra)
+    arrs = {}
+    for key in ("AVT", "BU", "AX", "BX", "G"):
+        _check_buf(bufs[key])
+        p = (ctypes.c_void_p * cnt)()
+        base = bufs[key].ctypes.data
+        for e in range(cnt):
+            p[e] = base + 8 * int(offs[key][e])
+        arrs[key] = p
+    dims = [np.ascontiguousarray(x, dtype=np.int32) for x in (ra, rb, k)]
+    return lib().oracle_lr_chain_batch(cnt, arrs["AVT"], arrs["BU"], arrs["AX"], arrs["BX"], arrs["G"],
+                                       *(d.ctypes.data for d in dims), nthreads)
 
 
 def max_threads() -> int:

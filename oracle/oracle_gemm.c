@@ -29,6 +29,7 @@
 #include <stddef.h>
 #include <stdint.h>
 #include <math.h>
+#include <stdlib.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -131,4 +132,79 @@ int oracle_max_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* The low-rank multiplication core of Alg. 1 (Sec. 3): for low-rank blocks
+ * A = A_U A_X A_{V^T} (rank ra) and B = B_U B_X B_{V^T} (rank rb),
+ *     C_temp = A_{V^T} B_U     (ra x rb, k-long inner dimension)
+ *     E_temp = A_X C_temp      (ra x rb)
+ *     G_XY   = E_temp B_X      (ra x rb), written (not accumulated),
+ * each step the plain product above (oracle_gemm into a zeroed target).
+ * `work` holds 2 ra rb doubles. */
+void oracle_lr_chain(int32_t ra, int32_t rb, int32_t k,
+                     const double* AVT, int32_t ld_avt,
+                     const double* BU, int32_t ld_bu,
+                     const double* AX, int32_t ld_ax,
+                     const double* BX, int32_t ld_bx,
+                     double* G, int32_t ldg, double* work)
+{
+    double* Ct = work;
+    double* Et = work + (size_t)ra * (size_t)rb;
+    for (size_t i = 0; i < 2 * (size_t)ra * (size_t)rb; ++i) work[i] = 0.0;
+    oracle_gemm(ra, rb, k, AVT, ld_avt, BU, ld_bu, Ct, ra);
+    oracle_gemm(ra, rb, ra, AX, ld_ax, Ct, ra, Et, ra);
+    for (int32_t j = 0; j < rb; ++j)
+        for (int32_t i = 0; i < ra; ++i) G[(size_t)i + (size_t)j * (size_t)ldg] = 0.0;
+    oracle_gemm(ra, rb, rb, Et, ra, BX, ld_bx, G, ldg);
+}
+
+/* A batch of chains: pointer arrays AVT, BU, AX, BX, G and per-entry
+ * (ra, rb, k) with tight leading dimensions (ra, k, ra, rb, ra).
+ * Parallel over entries; returns the thread count used. */
+int oracle_lr_chain_batch(int64_t count,
+                          const double* const* AVT, const double* const* BU,
+                          const double* const* AX, const double* const* BX,
+                          double* const* G,
+                          const int32_t* ra, const int32_t* rb, const int32_t* k,
+                          int nthreads)
+{
+    int used = 1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+    {
+#pragma omp single
+        used = omp_get_num_threads();
+        double* work = 0;
+        size_t cap = 0;
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t e = 0; e < count; ++e) {
+            size_t need = 2 * (size_t)ra[e] * (size_t)rb[e];
+            if (need > cap) {
+                free(work);
+                work = (double*)malloc(need * sizeof(double));
+                cap = need;
+            }
+            oracle_lr_chain(ra[e], rb[e], k[e], AVT[e], ra[e], BU[e], k[e], AX[e], ra[e], BX[e], rb[e],
+                            G[e], ra[e], work);
+        }
+        free(work);
+    }
+#else
+    (void)nthreads;
+    double* work = 0;
+    size_t cap = 0;
+    for (int64_t e = 0; e < count; ++e) {
+        size_t need = 2 * (size_t)ra[e] * (size_t)rb[e];
+        if (need > cap) {
+            free(work);
+            work = (double*)malloc(need * sizeof(double));
+            cap = need;
+        }
+        oracle_lr_chain(ra[e], rb[e], k[e], AVT[e], ra[e], BU[e], k[e], AX[e], ra[e], BX[e], rb[e], G[e], ra[e],
+                        work);
+    }
+    free(work);
+#endif
+    return used;
 }

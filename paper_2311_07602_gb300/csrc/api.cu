@@ -234,6 +234,13 @@ struct lrb_plan {
     bool launched = false;
     lrb_plan_info info{};
     split::SplitPlan* sp = nullptr;
+    // low-rank chain plans
+    int lr_kind = 0;                   // 0: none, 1: fused, 2: unfused (three batched products)
+    LrDesc* d_lr = nullptr;
+    int lr_count = 0;
+    void* lr_work = nullptr;           // unfused: C_temp and E_temp of every block
+    size_t lr_work_bytes = 0;
+    lrb_plan* lr_stage[3] = {nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -404,6 +411,12 @@ lrb_status choose_variants(lrb_handle* h, const lrb_gemm_desc* d, size_t count, 
 
 void free_plan(lrb_plan* p) {
     if (!p) return;
+    for (lrb_plan*& q : p->lr_stage)
+        if (q) {
+            free_plan(q);
+            q = nullptr;
+        }
+    if (p->lr_work) cudaFree(p->lr_work);
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
     if (p->sp) split::destroy(p->sp);
@@ -559,7 +572,7 @@ lrb_status lrb_plan_create(lrb_handle* h, const lrb_gemm_desc* host_descs, size_
     p->info.precision = o.precision;
 
     if (o.precision >= LRB_PREC_SPLIT_BF16_S3) {
-        s = split::create(h->device, h->sms, p->descs.data(), count, o.precision, &p->sp, &p->info);
+        s = split::create(h->device, h->sms, p->descs.data(), count, o.precision, &p->sp, &p->info, o.test_stall);
         if (s != LRB_OK) {
             free_plan(p);
             return s;
@@ -672,6 +685,19 @@ lrb_status lrb_launch(lrb_plan* p, void* stream) {
         cudaError_t e = split::launch(p->sp, s);
         return e == cudaSuccess ? LRB_OK : cuda_fail(e, "split launch");
     }
+    if (p->lr_kind == 1) {
+        cudaError_t e = launch_lr_chain(p->d_lr, p->lr_count, s);
+        return e == cudaSuccess ? LRB_OK : cuda_fail(e, "low-rank chain launch");
+    }
+    if (p->lr_kind == 2) {
+        LRB_CUDA(cudaMemsetAsync(p->lr_work, 0, p->lr_work_bytes, s));
+        LRB_CUDA(launch_lr_zero(p->d_lr, p->lr_count, s));
+        for (lrb_plan* q : p->lr_stage) {
+            lrb_status st = lrb_launch(q, stream);
+            if (st != LRB_OK) return st;
+        }
+        return LRB_OK;
+    }
     cudaError_t e = p->use_graph ? cudaGraphLaunch(p->exec, s)
                                  : launch_persistent(p->d_descs, p->d_items, p->n_items, p->d_head, p->grid, s, p->wide);
     if (e != cudaSuccess) return cuda_fail(e, "persistent launch");
@@ -681,6 +707,7 @@ lrb_status lrb_launch(lrb_plan* p, void* stream) {
 lrb_status lrb_launch_plain(lrb_plan* p, void* stream) {
     if (!p) return fail(LRB_ERR_INVALID, "plan is NULL");
     if (p->sp) return fail(LRB_ERR_UNSUPPORTED, "split-precision plans have no plain launch");
+    if (p->lr_kind) return fail(LRB_ERR_UNSUPPORTED, "low-rank chain plans have no plain launch");
     cudaStream_t s = (cudaStream_t)stream;
     LRB_CUDA(cudaSetDevice(p->h->device));
     p->last_stream = s;
@@ -888,6 +915,98 @@ lrb_status lrb_split_dump_levels(lrb_plan* p, float* dump, void* stream) {
     p->launched = true;
     cudaError_t e = split::launch_dump(p->sp, dump, s);
     return e == cudaSuccess ? LRB_OK : cuda_fail(e, "split dump launch");
+}
+
+lrb_status lrb_lr_plan_create(lrb_handle* h, const lrb_lr_desc* d, size_t count, int32_t fused, lrb_plan** out) {
+    if (!h || !out) return fail(LRB_ERR_INVALID, "NULL argument");
+    *out = nullptr;
+    if (!d) return fail(LRB_ERR_INVALID, "host_descs is NULL");
+    if (count == 0) return fail(LRB_ERR_INVALID, "count is 0");
+    if (count > 0x7fffffffull) return fail(LRB_ERR_INVALID, "count exceeds 2^31-1");
+    double flops = 0, bytes = 0;
+    for (size_t e = 0; e < count; ++e) {
+        const lrb_lr_desc& x = d[e];
+        char buf[160];
+        if (!x.AVT || !x.BU || !x.AX || !x.BX || !x.G) {
+            std::snprintf(buf, sizeof buf, "entry %zu: NULL operand pointer", e);
+            return fail(LRB_ERR_INVALID, buf);
+        }
+        if (((uintptr_t)x.AVT | (uintptr_t)x.BU | (uintptr_t)x.AX | (uintptr_t)x.BX | (uintptr_t)x.G) & 7u) {
+            std::snprintf(buf, sizeof buf, "entry %zu: operand pointer not 8-byte aligned", e);
+            return fail(LRB_ERR_INVALID, buf);
+        }
+        if (x.ra <= 0 || x.rb <= 0 || x.k <= 0 || x.ld_avt < x.ra || x.ld_bu < x.k || x.ld_ax < x.ra ||
+            x.ld_bx < x.rb || x.ldg < x.ra) {
+            std::snprintf(buf, sizeof buf, "entry %zu: bad dimension or leading dimension", e);
+            return fail(LRB_ERR_INVALID, buf);
+        }
+        Range r;
+        if (!extent(x.AVT, x.ra, x.k, x.ld_avt, &r) || !extent(x.BU, x.k, x.rb, x.ld_bu, &r) ||
+            !extent(x.AX, x.ra, x.ra, x.ld_ax, &r) || !extent(x.BX, x.rb, x.rb, x.ld_bx, &r) ||
+            !extent(x.G, x.ra, x.rb, x.ldg, &r)) {
+            std::snprintf(buf, sizeof buf, "entry %zu: operand extent overflows", e);
+            return fail(LRB_ERR_INVALID, buf);
+        }
+        if (fused && (x.ra > lr_chain_max_rank() || x.rb > lr_chain_max_rank()))
+            return fail(LRB_ERR_UNSUPPORTED, "fused low-rank chain supports ranks up to 64");
+        const double ra = x.ra, rb = x.rb, k = x.k;
+        flops += ra * rb * (2 * k + 2 * ra + 2 * rb);
+        bytes += 8 * (ra * k + k * rb + ra * ra + rb * rb + ra * rb);
+    }
+    LRB_CUDA(cudaSetDevice(h->device));
+    lrb_plan* p = new (std::nothrow) lrb_plan();
+    if (!p) return fail(LRB_ERR_NOMEM, "plan allocation");
+    p->h = h;
+    p->lr_kind = fused ? 1 : 2;
+    p->lr_count = (int)count;
+    p->info.entries = (int64_t)count;
+    p->info.flops = flops;
+    p->info.alg_bytes = bytes;
+    p->info.precision = LRB_PREC_FP64;
+    p->info.grid = (int)count;
+    cudaError_t ce = cudaMalloc(&p->dmem, sizeof(LrDesc) * count);
+    if (ce == cudaSuccess) ce = cudaMemcpy(p->dmem, d, sizeof(LrDesc) * count, cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) {
+        free_plan(p);
+        return cuda_fail(ce, "chain plan upload");
+    }
+    p->d_lr = (LrDesc*)p->dmem;
+    if (!fused) {
+        size_t elems = 0;
+        for (size_t e = 0; e < count; ++e) elems += 2 * (size_t)d[e].ra * d[e].rb;
+        p->lr_work_bytes = elems * 8;
+        ce = cudaMalloc(&p->lr_work, p->lr_work_bytes);
+        if (ce != cudaSuccess) {
+            free_plan(p);
+            return fail(LRB_ERR_NOMEM, "chain temporaries");
+        }
+        std::vector<lrb_gemm_desc> s1(count), s2(count), s3(count);
+        double* w = (double*)p->lr_work;
+        for (size_t e = 0; e < count; ++e) {
+            const lrb_lr_desc& x = d[e];
+            double* Ct = w;
+            double* Et = w + (size_t)x.ra * x.rb;
+            w += 2 * (size_t)x.ra * x.rb;
+            s1[e] = lrb_gemm_desc{x.AVT, x.BU, Ct, x.ra, x.rb, x.k, x.ld_avt, x.ld_bu, x.ra};
+            s2[e] = lrb_gemm_desc{x.AX, Ct, Et, x.ra, x.rb, x.ra, x.ld_ax, x.ra, x.ra};
+            s3[e] = lrb_gemm_desc{Et, x.BX, x.G, x.ra, x.rb, x.rb, x.ra, x.ld_bx, x.ldg};
+        }
+        lrb_plan_opts o = default_opts();
+        o.use_graph = 1;
+        o.check_alias = 0;
+        const std::vector<lrb_gemm_desc>* st[3] = {&s1, &s2, &s3};
+        for (int i = 0; i < 3; ++i) {
+            lrb_status r = lrb_plan_create(h, st[i]->data(), count, &o, &p->lr_stage[i]);
+            if (r != LRB_OK) {
+                free_plan(p);
+                return r;
+            }
+        }
+        p->info.items = p->lr_stage[0]->info.items + p->lr_stage[1]->info.items + p->lr_stage[2]->info.items;
+        p->info.groups = 3;
+    }
+    *out = p;
+    return LRB_OK;
 }
 
 lrb_status lrb_plan_get_info(const lrb_plan* p, lrb_plan_info* info) {

@@ -17,6 +17,18 @@ struct DevDesc {
 };
 static_assert(sizeof(DevDesc) == sizeof(lrb_gemm_desc), "descriptor layout");
 
+// Device copy of one low-rank chain entry (same layout as lrb_lr_desc).
+struct LrDesc {
+    const double* AVT;
+    const double* BU;
+    const double* AX;
+    const double* BX;
+    double* G;
+    int32_t ra, rb, k;
+    int32_t ld_avt, ld_bu, ld_ax, ld_bx, ldg;
+};
+static_assert(sizeof(LrDesc) == sizeof(lrb_lr_desc), "chain descriptor layout");
+
 // One output tile of one entry: rows [row0, row0+BM), cols [col0, col0+BN)
 // of the variant's tile extent (clipped to the entry at run time).
 struct Item {
@@ -57,6 +69,12 @@ cudaError_t launch_plain_group(int variant, const DevDesc* d_descs, const int32_
                                int n_entries, int tiles_m, int tiles_n, cudaStream_t s);
 int persistent_blocks_per_sm(bool wide = false);
 bool variant_is_narrow(int v);
+
+// Fused low-rank chain (lr_chain.cu).
+size_t lr_chain_smem_bytes();
+int lr_chain_max_rank();
+cudaError_t launch_lr_chain(const LrDesc* d_descs, int count, cudaStream_t s);
+cudaError_t launch_lr_zero(const LrDesc* d_descs, int count, cudaStream_t s);
 
 // Sets the calling thread's lrb_last_error() message (api.cu).
 void set_last_error(const char* msg);

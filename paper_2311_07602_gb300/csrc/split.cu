@@ -124,6 +124,9 @@ __device__ __forceinline__ int exp_of_bits(unsigned long long mag) {
 }
 
 // Balanced digits of a given the chunk exponent E (see file comment).
+// Z = RN_even(M 2^-sh) is formed with 64-bit integer shifts of the
+// significand; the lowest digit comes off the 64-bit Z, the rest in 32-bit
+// arithmetic (after one digit |Z| < 2^(beta (S-1) + 1) <= 2^28).
 template <int S, int BETA>
 __device__ __forceinline__ void make_digits(double a, int E, int (&d)[S]) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(a);
@@ -135,26 +138,34 @@ __device__ __forceinline__ void make_digits(double a, int E, int (&d)[S]) {
         const int e = (ef ? ef : 1) - 1075;                 // a = M 2^e
         const int sh = E - BETA * S - e;                     // Z = RN(M 2^-sh)
         if (sh <= 0) {
-            Z = (long long)(M << (-sh));
+            Z = (long long)(M << (-sh));                     // subnormal rows only
         } else if (sh < 64) {
             const unsigned long long half = 1ull << (sh - 1);
             Z = (long long)((M + half - 1 + ((M >> sh) & 1ull)) >> sh);
         }
         if (bits >> 63) Z = -Z;
     }
-    constexpr long long base = 1ll << BETA, h = 1ll << (BETA - 1);
+    constexpr int base = 1 << BETA, h = 1 << (BETA - 1);
+    // lowest digit from the 64-bit value (its low word suffices for the digit)
+    const int d_last = (((int)(unsigned)Z + h) & (base - 1)) - h;
+    d[S - 1] = d_last;
+    int z = (int)((Z - d_last) >> BETA);
 #pragma unroll
-    for (int s = S - 1; s >= 1; --s) {
-        const long long dig = ((Z + h) & (base - 1)) - h;
-        d[s] = (int)dig;
-        Z = (Z - dig) >> BETA;
+    for (int s = S - 2; s >= 1; --s) {
+        const int dig = ((z + h) & (base - 1)) - h;
+        d[s] = dig;
+        z = (z - dig) >> BETA;
     }
-    d[0] = (int)Z;
+    d[0] = z;
 }
 
+// 16-bit pattern of an integer digit |d| <= 2^(beta) (exact in either type).
+// BF16: the float 1.5 * 2^23 + d, formed by an integer add to its bit
+// pattern and the constant subtracted in float, is exactly d; its top 16 bits
+// are the bf16 pattern.
 template <bool FP16>
 __device__ __forceinline__ uint16_t digit_bits(int d) {
-    const float f = (float)d;   // |d| <= 2^(beta): exact in float and in the 16-bit type
+    const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
     if constexpr (FP16) {
         return __half_as_ushort(__float2half_rn(f));
     } else {
@@ -184,7 +195,8 @@ __device__ __forceinline__ double scaled_int_to_double(long long I, int X) {
 template <bool FP16, int S>
 __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restrict__ descs,
                                                          const SItem* __restrict__ items, int n_items,
-                                                         int* __restrict__ status, float* __restrict__ dump) {
+                                                         int* __restrict__ status, float* __restrict__ dump,
+                                                         int test_stall) {
     using C_ = Cfg<FP16, S>;
     constexpr int BETA = C_::beta, KC = C_::kc;
     constexpr int QC = KC / 4;            // chunk columns of A per thread
@@ -194,6 +206,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
     __shared__ int s_E[2][kTM];
     __shared__ int s_F[2][kTN];
     __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ __align__(8) uint64_t s_never;   // test_stall: a barrier nothing arrives on
     __shared__ uint32_t s_tmem;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -208,6 +221,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s_bar[0])));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s_bar[1])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s_never)));
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -239,39 +253,42 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
     auto recombine = [&](uint32_t parity) -> bool {
         // warp-uniform decision before the warp-collective TMEM loads
         if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&s_bar[prev.stage]), parity))) return false;
+        if (test_stall && !__all_sync(0xffffffffu, mbar_wait(smem_u32(&s_never), 0))) return false;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        uint32_t v[S][16];
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-#pragma unroll
-        for (int l = 0; l < S; ++l) {
-            const uint32_t ta = tmem + lane_base + (uint32_t)(prev.stage * S * kTN + l * kTN + 16 * q);
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                "[%16];\n"
-                : "=r"(v[l][0]), "=r"(v[l][1]), "=r"(v[l][2]), "=r"(v[l][3]), "=r"(v[l][4]), "=r"(v[l][5]),
-                  "=r"(v[l][6]), "=r"(v[l][7]), "=r"(v[l][8]), "=r"(v[l][9]), "=r"(v[l][10]), "=r"(v[l][11]),
-                  "=r"(v[l][12]), "=r"(v[l][13]), "=r"(v[l][14]), "=r"(v[l][15])
-                : "r"(ta));
-        }
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         const int E = s_E[prev.stage][rloc];
         const int row = prev.row0 + rloc;
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-            const int j = 16 * q + jj;
-            long long I = 0;
+        for (int half = 0; half < 2; ++half) {
+            uint32_t v[S][8];
 #pragma unroll
-            for (int l = 0; l < S; ++l)   // level L = l + 2, weight 2^(beta (S - 1 - l))
-                I = (I << BETA) + (long long)__float2int_rn(__uint_as_float(v[l][jj]));
-            if (dump != nullptr && row < prev.d.m && prev.col0 + j < prev.d.n) {
-#pragma unroll
-                for (int l = 0; l < S; ++l)
-                    dump[(((size_t)prev.c * S + l) * prev.d.m + row) * prev.d.n + (prev.col0 + j)] =
-                        __uint_as_float(v[l][jj]);
+            for (int l = 0; l < S; ++l) {
+                const uint32_t ta = tmem + lane_base + (uint32_t)(prev.stage * S * kTN + l * kTN + 16 * q + 8 * half);
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                             : "=r"(v[l][0]), "=r"(v[l][1]), "=r"(v[l][2]), "=r"(v[l][3]), "=r"(v[l][4]),
+                               "=r"(v[l][5]), "=r"(v[l][6]), "=r"(v[l][7])
+                             : "r"(ta));
             }
-            acc[jj] += scaled_int_to_double(I, E + s_F[prev.stage][j] - BETA * (S + 1));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+                const int j = 16 * q + 8 * half + jj;
+                long long I = 0;
+#pragma unroll
+                for (int l = 0; l < S; ++l)   // level L = l + 2, weight 2^(beta (S - 1 - l))
+                    I = (I << BETA) + (long long)__float2int_rn(__uint_as_float(v[l][jj]));
+                if (dump != nullptr && row < prev.d.m && prev.col0 + j < prev.d.n) {
+#pragma unroll
+                    for (int l = 0; l < S; ++l)
+                        dump[(((size_t)prev.c * S + l) * prev.d.m + row) * prev.d.n + (prev.col0 + j)] =
+                            __uint_as_float(v[l][jj]);
+                }
+                // the exact binary64 value I 2^X (built from bits with integer
+                // instructions), then one binary64 add
+                acc[8 * half + jj] += scaled_int_to_double(I, E + s_F[prev.stage][j] - BETA * (S + 1));
+            }
         }
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         return true;
     };
 
@@ -476,7 +493,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
 
 template <bool FP16, int S>
 cudaError_t launch_t(const DevDesc* descs, const SItem* items, int n_items, int* status, float* dump,
-                     cudaStream_t s) {
+                     int test_stall, cudaStream_t s) {
     const int smem = Cfg<FP16, S>::smem;
     cudaError_t e = cudaFuncSetAttribute(k_split<FP16, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
@@ -485,17 +502,17 @@ cudaError_t launch_t(const DevDesc* descs, const SItem* items, int n_items, int*
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = std::max(1, std::min(n_items, sms));
-    k_split<FP16, S><<<grid, kThreadsS, smem, s>>>(descs, items, n_items, status, dump);
+    k_split<FP16, S><<<grid, kThreadsS, smem, s>>>(descs, items, n_items, status, dump, test_stall);
     return cudaGetLastError();
 }
 
 cudaError_t launch_prec(int precision, const DevDesc* descs, const SItem* items, int n_items, int* status,
-                        float* dump, cudaStream_t s) {
+                        float* dump, int test_stall, cudaStream_t s) {
     switch (precision) {
-        case LRB_PREC_SPLIT_BF16_S3: return launch_t<false, 3>(descs, items, n_items, status, dump, s);
-        case LRB_PREC_SPLIT_BF16_S4: return launch_t<false, 4>(descs, items, n_items, status, dump, s);
-        case LRB_PREC_SPLIT_FP16_S3: return launch_t<true, 3>(descs, items, n_items, status, dump, s);
-        case LRB_PREC_SPLIT_FP16_S4: return launch_t<true, 4>(descs, items, n_items, status, dump, s);
+        case LRB_PREC_SPLIT_BF16_S3: return launch_t<false, 3>(descs, items, n_items, status, dump, test_stall, s);
+        case LRB_PREC_SPLIT_BF16_S4: return launch_t<false, 4>(descs, items, n_items, status, dump, test_stall, s);
+        case LRB_PREC_SPLIT_FP16_S3: return launch_t<true, 3>(descs, items, n_items, status, dump, test_stall, s);
+        case LRB_PREC_SPLIT_FP16_S4: return launch_t<true, 4>(descs, items, n_items, status, dump, test_stall, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -504,6 +521,7 @@ cudaError_t launch_prec(int precision, const DevDesc* descs, const SItem* items,
 
 struct SplitPlan {
     int precision = 0;
+    int test_stall = 0;
     void* dmem = nullptr;
     DevDesc* d_descs = nullptr;
     SItem* d_items = nullptr;
@@ -519,7 +537,7 @@ int digit_count(int precision) {
 }
 
 lrb_status create(int device, int sms, const lrb_gemm_desc* descs, size_t count, int precision, SplitPlan** out,
-                  lrb_plan_info* info) {
+                  lrb_plan_info* info, int test_stall) {
     (void)device;
     (void)sms;
     *out = nullptr;
@@ -533,6 +551,7 @@ lrb_status create(int device, int sms, const lrb_gemm_desc* descs, size_t count,
     }
     SplitPlan* p = new SplitPlan();
     p->precision = precision;
+    p->test_stall = test_stall;
     const size_t o_items = ((sizeof(DevDesc) * count + 255) / 256) * 256;
     const size_t o_status = o_items + ((sizeof(SItem) * std::max<size_t>(items.size(), 1) + 255) / 256) * 256;
     cudaError_t ce = cudaMalloc(&p->dmem, o_status + 256);
@@ -566,11 +585,11 @@ lrb_status create(int device, int sms, const lrb_gemm_desc* descs, size_t count,
 }
 
 cudaError_t launch(SplitPlan* p, cudaStream_t s) {
-    return launch_prec(p->precision, p->d_descs, p->d_items, p->n_items, p->d_status, nullptr, s);
+    return launch_prec(p->precision, p->d_descs, p->d_items, p->n_items, p->d_status, nullptr, p->test_stall, s);
 }
 
 cudaError_t launch_dump(SplitPlan* p, float* dump, cudaStream_t s) {
-    return launch_prec(p->precision, p->d_descs, p->d_items, p->n_items, p->d_status, dump, s);
+    return launch_prec(p->precision, p->d_descs, p->d_items, p->n_items, p->d_status, dump, p->test_stall, s);
 }
 
 int read_status(SplitPlan* p, cudaStream_t s, int* value) {

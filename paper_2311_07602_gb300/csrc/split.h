@@ -12,7 +12,7 @@ struct SplitPlan;
 // Builds the device work list for `count` entries at `precision`
 // (LRB_PREC_SPLIT_*); fills items/grid/groups of *info.
 lrb_status create(int device, int sms, const lrb_gemm_desc* descs, size_t count, int precision, SplitPlan** out,
-                  lrb_plan_info* info);
+                  lrb_plan_info* info, int test_stall = 0);
 cudaError_t launch(SplitPlan* p, cudaStream_t s);
 // Same launch, also writing every chunk's FP32 level sums to `dump`
 // (float[chunks][S][m][n] for a single-entry plan) for the exactness test.

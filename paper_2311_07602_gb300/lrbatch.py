@@ -28,6 +28,13 @@ LRB_PREC_FP64, LRB_PREC_FP64_DMMA_ALLOWED, LRB_PREC_SPLIT_BF16_S3, LRB_PREC_SPLI
 SPLIT_PRECISIONS = {"bf16_s3": LRB_PREC_SPLIT_BF16_S3, "bf16_s4": LRB_PREC_SPLIT_BF16_S4,
                     "fp16_s3": LRB_PREC_SPLIT_FP16_S3, "fp16_s4": LRB_PREC_SPLIT_FP16_S4}
 
+# lrb_lr_desc: five pointers then eight int32 (72 bytes)
+LR_DESC_DTYPE = np.dtype([("AVT", np.uint64), ("BU", np.uint64), ("AX", np.uint64), ("BX", np.uint64),
+                          ("G", np.uint64), ("ra", np.int32), ("rb", np.int32), ("k", np.int32),
+                          ("ld_avt", np.int32), ("ld_bu", np.int32), ("ld_ax", np.int32), ("ld_bx", np.int32),
+                          ("ldg", np.int32)])
+assert LR_DESC_DTYPE.itemsize == 72
+
 # lrb_gemm_desc: three pointers then six int32 (48 bytes, no padding)
 DESC_DTYPE = np.dtype([("A", np.uint64), ("B", np.uint64), ("C", np.uint64), ("m", np.int32), ("n", np.int32),
                        ("k", np.int32), ("lda", np.int32), ("ldb", np.int32), ("ldc", np.int32)])
@@ -37,7 +44,7 @@ assert DESC_DTYPE.itemsize == 48
 class lrb_plan_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("tune", ctypes.c_int32),
                 ("force_variant", ctypes.c_int32), ("check_alias", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("test_stall", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class lrb_plan_info(ctypes.Structure):
@@ -83,6 +90,7 @@ def lib():
             "lrb_execute_host": ([vp, vp, sz, ctypes.POINTER(lrb_plan_opts), vp], i32),
             "lrb_launch_noalloc": ([vp, sz, vp], i32),
             "lrb_plan_status": ([vp], i32),
+            "lrb_lr_plan_create": ([vp, vp, sz, i32, ctypes.POINTER(vp)], i32),
             "lrb_queue_create": ([vp, sz, ctypes.c_int, ctypes.POINTER(vp)], i32),
             "lrb_queue_set_limits": ([vp, sz, sz], i32),
             "lrb_queue_submit": ([vp, vp, sz, ctypes.POINTER(ctypes.c_uint64)], i32),
@@ -121,8 +129,10 @@ def check(status):
         raise LrbError(status, last_error())
 
 
-def make_opts(precision=LRB_PREC_FP64, use_graph=False, tune=True, force_variant=-1, check_alias=True):
+def make_opts(precision=LRB_PREC_FP64, use_graph=False, tune=True, force_variant=-1, check_alias=True,
+              test_stall=False):
     o = lrb_plan_opts()
+    o.test_stall = int(bool(test_stall))
     o.precision = precision
     o.use_graph = int(bool(use_graph))
     o.tune = int(bool(tune))
@@ -139,6 +149,17 @@ def descs_for(batch) -> np.ndarray:
     d["C"] = np.uint64(batch.C.data_ptr()) + 8 * batch.offC.astype(np.uint64)
     for key in ("m", "n", "k", "lda", "ldb", "ldc"):
         d[key] = getattr(batch, key)
+    return d
+
+
+def lr_descs_for(lb) -> np.ndarray:
+    """lrb_lr_desc rows for a workloads.LrBatch whose buffers are tensors."""
+    d = np.zeros(len(lb), dtype=LR_DESC_DTYPE)
+    for key in ("AVT", "BU", "AX", "BX", "G"):
+        d[key] = np.uint64(lb.bufs[key].data_ptr()) + 8 * lb.offs[key].astype(np.uint64)
+    d["ra"], d["rb"], d["k"] = lb.ra, lb.rb, lb.k
+    d["ld_avt"], d["ld_bu"], d["ld_ax"], d["ld_bx"], d["ldg"] = (lb.ra + lb.pad, lb.k + lb.pad, lb.ra + lb.pad,
+                                                                 lb.rb + lb.pad, lb.ra + lb.pad)
     return d
 
 
@@ -221,13 +242,19 @@ class Handle:
 
 
 class Plan:
-    """lrb_plan_create / lrb_launch / lrb_launch_plain / lrb_plan_destroy."""
+    """lrb_plan_create / lrb_launch / lrb_launch_plain / lrb_plan_destroy
+    (lrb_lr_plan_create when lr_fused is given: descs are lrb_lr_desc rows)."""
 
-    def __init__(self, handle: Handle, descs: np.ndarray, **opts):
+    def __init__(self, handle: Handle, descs: np.ndarray, lr_fused=None, **opts):
         self.handle = handle
+        self.ptr = ctypes.c_void_p()
+        if lr_fused is not None:
+            self.descs = np.ascontiguousarray(descs, dtype=LR_DESC_DTYPE)
+            check(lib().lrb_lr_plan_create(handle.ptr, self.descs.ctypes.data, len(self.descs), int(bool(lr_fused)),
+                                           ctypes.byref(self.ptr)))
+            return
         self.descs = np.ascontiguousarray(descs, dtype=DESC_DTYPE)
         self.opts = make_opts(**opts)
-        self.ptr = ctypes.c_void_p()
         check(lib().lrb_plan_create(handle.ptr, self.descs.ctypes.data, len(self.descs), ctypes.byref(self.opts),
                                     ctypes.byref(self.ptr)))
 

@@ -207,3 +207,51 @@ def serving_requests(count: int, rate: float, seed: int = 5, max_products: int =
         form = rng.integers(0, 2, cnt).astype(np.int32)
         reqs.append((form, b, r))
     return arrivals, reqs
+
+
+@dataclass
+class LrBatch:
+    """Batched low-rank chain inputs: per entry A_{V^T} (ra x k), B_U (k x rb),
+    A_X (ra x ra), B_X (rb x rb) and the output G (ra x rb), each in its own
+    flat buffer, entries back to back, leading dimensions = rows + pad."""
+    bufs: dict
+    offs: dict
+    ra: np.ndarray
+    rb: np.ndarray
+    k: np.ndarray
+    pad: int = 0
+
+    def __len__(self):
+        return len(self.ra)
+
+    def flops_paper(self) -> float:
+        """The paper's count, batch (4 r^3 + 2 r^2 b) for ra = rb = r (Sec. 7, GFLOPS equation)."""
+        r = self.ra.astype(np.float64)
+        return float(np.sum(4 * r ** 3 + 2 * r ** 2 * self.k))
+
+    def to(self, device) -> "LrBatch":
+        return LrBatch({key: t.to(device) for key, t in self.bufs.items()}, self.offs, self.ra, self.rb, self.k,
+                       self.pad)
+
+
+def lr_batch(batch: int, b: int, r: int, *, rb: int = None, seed: int = 0, device="cpu", pad: int = 0,
+             dist: str = "normal") -> LrBatch:
+    """`batch` low-rank chains with rank r (and rb, default r) and block size
+    b, entries N(0,1) (the paper's experiments use normally distributed
+    entries, Sec. 7), drawn in the order A_{V^T}, B_U, A_X, B_X from one
+    generator seeded with `seed`."""
+    rb = r if rb is None else rb
+    shapes = {"AVT": (r, b), "BU": (b, rb), "AX": (r, r), "BX": (rb, rb), "G": (r, rb)}
+    g = _gen(seed, device)
+    bufs, offs = {}, {}
+    for key, (rows, cols) in shapes.items():
+        size = (rows + pad) * cols
+        t = torch.empty(batch * size, dtype=torch.float64, device=device)
+        if key == "G":
+            t.zero_()
+        else:
+            _fill(t, dist, g)
+        bufs[key] = t
+        offs[key] = np.arange(batch, dtype=np.int64) * size
+    full = lambda v: np.full(batch, v, dtype=np.int32)
+    return LrBatch(bufs, offs, full(r), full(rb), full(b), pad)

@@ -6,6 +6,7 @@ gamma_{k+1} of the exact value for any summation order).  Integer-valued,
 identity and permutation inputs are exact in any order, so there the check
 is bitwise.
 """
+import ctypes
 import math
 
 import numpy as np
@@ -246,3 +247,14 @@ def test_execute_host_pipelined_pieces(handle):
     handle.execute_host(d_big)                     # and again: cached plans
     exp3 = oracle_batch(Ah, Bh, oracle_batch(Ah, Bh, exp1, big), big)
     check_entries(pinned[2].numpy().copy(), exp3, Ah, Bh, exp1, big, tol=3e-13)
+
+
+def test_allocation_failure_is_reported(handle):
+    """A host-buffer batch whose device arena cannot exist (720 GB) fails with
+    LRB_ERR_NOMEM before any copy touches the (fake) host pointers."""
+    d = np.zeros(1, dtype=L.DESC_DTYPE)
+    d[0] = (0x10000000, 0x20000000, 0x30000000, 300000, 300000, 1, 300000, 1, 300000)
+    o = L.make_opts(check_alias=False)
+    st = L.lib().lrb_execute_host(handle.ptr, d.ctypes.data, 1, ctypes.byref(o), None)
+    assert st == L.LRB_ERR_NOMEM
+    assert "arena" in L.last_error()

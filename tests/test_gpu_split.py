@@ -169,3 +169,29 @@ def test_full_size_sampled(handle, name, form):
     assert np.all(np.abs(got - exp) <= 4 * oracle.gamma(nadd) * mag)
     del b
     torch.cuda.empty_cache()
+
+
+def test_bounded_wait_expiry_reports_timeout(handle):
+    """Failure path without a GPU fault: with test_stall the kernel also waits
+    on a barrier nothing arrives on; its 2 s bound expires, it drains its own
+    tensor-core work, frees TMEM, leaves its C tiles unwritten and sets the
+    plan's status word; the context stays usable for the next plan."""
+    b = wide(ragged_batch([(128, 64, 130), (100, 64, 200)], pad=0, seed=71))
+    Ah, Bh, C0 = host(b.A), host(b.B), host(b.C)
+    dev = b.to("cuda")
+    with handle.plan(L.descs_for(dev), precision=PREC["bf16_s3"], test_stall=True) as plan:
+        plan.launch()
+        assert plan.status() == L.LRB_ERR_TIMEOUT
+    assert np.array_equal(host(dev.C).view(np.uint64), C0.view(np.uint64))
+    dev2 = b.to("cuda")
+    with handle.plan(L.descs_for(dev2), precision=PREC["bf16_s3"]) as plan:
+        plan.launch()
+        assert plan.status() == L.LRB_OK
+    p = PRESETS["bf16_s3"]
+    got = host(dev2.C)
+    for e in range(len(b)):
+        A, B, C = mats(b, e, Ah, Bh, C0)
+        exp = oracle.split_gemm(A, B, C, p)
+        g = entry_view(got, int(b.offC[e]), *C.shape, int(b.ldc[e]))
+        nadd = ((A.shape[1] + p.kc - 1) // p.kc) * (len(p.levels()) + 1)
+        assert np.all(np.abs(g - exp) <= 2 * oracle.gamma(nadd) * oracle.recombination_magnitude(A, B, C, p))
