@@ -186,6 +186,8 @@ def main():
                     help="comma-separated subset of the other workloads to run")
     ap.add_argument("--split-batch", type=int, default=2048, help="entries of the split-precision batch")
     ap.add_argument("--dmma-scale", type=float, default=0.25, help="batch-count scale of the DMMA comparison")
+    ap.add_argument("--lr-batch", type=int, default=20000, help="blocks per low-rank chain configuration")
+    ap.add_argument("--lr-ranks", default="8,16,32,96,128", help="ranks of the low-rank chain sweep")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="batch-count scale of every group (profiling runs use a small case)")
     args = ap.parse_args()
@@ -302,7 +304,7 @@ def main():
         del batches
         torch.cuda.empty_cache()
         line["extras"] = extras(L, handle, stream, dev, peak, timed, set(args.extras.split(",")), args.split_batch,
-                                args.dmma_scale)
+                                args.dmma_scale, args.lr_batch, tuple(int(x) for x in args.lr_ranks.split(",")))
 
     if not args.no_cpu and rank == 0 and world == 1:
         f, s, used, ents = cpu_baseline(args.cpu_fraction)
@@ -319,7 +321,8 @@ def main():
     return 0
 
 
-def extras(L, handle, stream, dev, peak_fp64, timed, which, split_batch, dmma_scale=0.25):
+def extras(L, handle, stream, dev, peak_fp64, timed, which, split_batch, dmma_scale=0.25, lr_batch=20000,
+           lr_ranks=(8, 16, 32, 96, 128)):
     """The other workloads, each with its own plan, 3 warm-up and 5 timed launches:
     the 64-entry O-form batch (L2 flushed before every launch: it fits in L2),
     the 20,000-entry variable-size batch (persistent vs one launch per shape),
@@ -345,7 +348,7 @@ def extras(L, handle, stream, dev, peak_fp64, timed, which, split_batch, dmma_sc
     if "dmma" in which:
         out["dmma"] = dmma_leg(L, handle, dev, peak_fp64, timed, dmma_scale)
     if "lr" in which:
-        out["lr_chain"] = lr_leg(L, handle, dev, peak_fp64, timed)
+        out["lr_chain"] = lr_leg(L, handle, dev, peak_fp64, timed, lr_batch, lr_ranks)
     return out
 
 
@@ -360,7 +363,7 @@ PAPER_LR_GFLOPS = {
 }
 
 
-def lr_leg(L, handle, dev, peak_fp64, timed, batch=20000):
+def lr_leg(L, handle, dev, peak_fp64, timed, batch=20000, ranks=(8, 16, 32, 96, 128)):
     """The paper's batched low-rank multiplication G = A_X (A_{V^T} B_U) B_X
     (Alg. 1-3): batch 20,000, b in {512, 1024, 2048}, r in {8, 16, 32}, N(0,1),
     fused (one CTA per block, temporaries on chip) against unfused (three
@@ -370,7 +373,7 @@ def lr_leg(L, handle, dev, peak_fp64, timed, batch=20000):
     import torch
     from paper_2311_07602_gb300 import workloads as W
     rows = []
-    for r in (8, 16, 32, 96, 128):
+    for r in ranks:
         for b in (512, 1024, 2048):
             lb = W.lr_batch(batch, b, r, seed=7000 + 10 * r + b // 512, device=dev)
             d = L.lr_descs_for(lb)
@@ -465,6 +468,13 @@ def variable_leg(L, handle, dev, peak_fp64, timed):
         "persistent_ms": round(ms_p / 5, 3), "plain_ms": round(ms_q / 5, 3), "plain_launches": int(info["groups"]),
         "tiles": int(info["items"]), "plan_s_incl_tuning": round(plan_s, 2)}
     p.close()
+    # the same variable-size batch in split precision (one persistent tcgen05 launch over all tiles)
+    for name, prec in (("split_bf16_s3", L.LRB_PREC_SPLIT_BF16_S3), ("split_bf16_s4", L.LRB_PREC_SPLIT_BF16_S4)):
+        with handle.plan(L.descs_for(vb), precision=prec) as ps:
+            ms_s, _ = timed(lambda s: ps.launch(s), 3, 3)
+            st = ps.status()
+        out[name] = {"gflops_fp64_equiv": round(f * 3 / ms_s / 1e6, 1), "ms": round(ms_s / 3, 3),
+                     "vs_fp64_persistent": round((ms_p / 5) / (ms_s / 3), 3), "status": int(st)}
     del vb
     torch.cuda.empty_cache()
     return out

@@ -256,6 +256,10 @@ lrb_status lrb_queue_create(lrb_handle* h, size_t hbm_budget_bytes, int max_infl
 /* Waiting-FIFO limit (default 4096 requests) and entries per wave (default
  * 65536; a larger request still forms a wave of its own). */
 lrb_status lrb_queue_set_limits(lrb_queue* q, size_t max_waiting, size_t max_wave_entries);
+/* Arithmetic of the waves formed from now on (lrb_precision; default FP64).
+ * Split-precision waves run the tcgen05 kernel; a bounded device wait that
+ * expires fails that wave's requests (LRB_ERR_DEVICE from wait/poll). */
+lrb_status lrb_queue_set_precision(lrb_queue* q, int32_t precision);
 lrb_status lrb_queue_submit(lrb_queue* q, const lrb_gemm_desc* host_descs, size_t n, uint64_t* ticket);
 /* LRB_OK when done, LRB_ERR_TIMEOUT while pending, LRB_ERR_DEVICE if it failed. */
 lrb_status lrb_queue_poll(lrb_queue* q, uint64_t ticket);

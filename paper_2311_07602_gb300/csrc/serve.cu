@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "lrb_internal.h"
+#include "split.h"
 
 using Clock = std::chrono::steady_clock;
 using namespace lrb;
@@ -56,6 +57,8 @@ struct Slot {
     cudaEvent_t done = nullptr;
     void* dmem = nullptr;
     size_t dmem_bytes = 0;
+    int* h_status = nullptr;   // pinned: split-kernel status of the wave in flight
+    bool split = false;        // the wave in flight runs in split precision
     std::vector<Request*> reqs;
     bool busy = false;
 };
@@ -81,6 +84,7 @@ struct lrb_queue {
     size_t peak_reserved = 0;
     size_t max_waiting = 4096;
     size_t max_wave_entries = 1 << 16;
+    int precision = LRB_PREC_FP64;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Request*> waiting;
@@ -103,9 +107,41 @@ struct lrb_queue {
 namespace {
 
 // Build and launch one wave on slot s (called without the queue lock).
-lrb_status launch_wave(lrb_queue* q, Slot& s) {
+lrb_status launch_split_wave(lrb_queue* q, Slot& s, const std::vector<lrb_gemm_desc>& all, int precision) {
+    (void)q;
+    std::vector<int4> items;
+    split::build_items(all.data(), all.size(), items);
+    auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t o_items = align(sizeof(DevDesc) * all.size());
+    const size_t o_status = o_items + align(sizeof(int4) * std::max<size_t>(items.size(), 1));
+    const size_t need = o_status + 256;
+    if (need > s.dmem_bytes) {
+        if (s.dmem) cudaFreeAsync(s.dmem, s.stream);
+        s.dmem = nullptr;
+        s.dmem_bytes = 0;
+        const size_t want = need + need / 2;
+        if (cudaMallocAsync(&s.dmem, want, s.stream) != cudaSuccess) return LRB_ERR_NOMEM;
+        s.dmem_bytes = want;
+    }
+    char* base = (char*)s.dmem;
+    int* d_status = (int*)(base + o_status);
+    cudaError_t e = cudaMemcpyAsync(base, all.data(), sizeof(DevDesc) * all.size(), cudaMemcpyHostToDevice, s.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + o_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice,
+                            s.stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, sizeof(int), s.stream);
+    if (e == cudaSuccess)
+        e = split::launch_raw(precision, (const DevDesc*)base, (const int4*)(base + o_items), (int)items.size(),
+                              d_status, s.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost, s.stream);
+    if (e == cudaSuccess) e = cudaEventRecord(s.done, s.stream);
+    return e == cudaSuccess ? LRB_OK : LRB_ERR_DEVICE;
+}
+
+lrb_status launch_wave(lrb_queue* q, Slot& s, int precision) {
     std::vector<lrb_gemm_desc> all;
     for (Request* r : s.reqs) all.insert(all.end(), r->descs.begin(), r->descs.end());
+    if (precision >= LRB_PREC_SPLIT_BF16_S3) return launch_split_wave(q, s, all, precision);
     lrb_plan_opts o = default_plan_opts();
     o.tune = 0;
     o.check_alias = 0;
@@ -155,16 +191,17 @@ void worker_main(lrb_queue* q) {
         uint64_t busy = 0;
         for (Slot& s : q->slots) {
             if (!s.busy) continue;
-            const cudaError_t e = cudaEventQuery(s.done);
+            cudaError_t e = cudaEventQuery(s.done);
             if (e == cudaErrorNotReady) {
                 ++busy;
                 continue;
             }
             const Clock::time_point now = Clock::now();
+            const bool wait_expired = e == cudaSuccess && s.split && *s.h_status != 0;
             for (Request* r : s.reqs) {
                 q->reserved -= r->bytes;
                 r->latency_ms = ms_between(r->t_submit, now);
-                if (e == cudaSuccess) {
+                if (e == cudaSuccess && !wait_expired) {
                     r->state = kDone;
                     ++q->completed;
                     q->lat.push_back(r->latency_ms);
@@ -175,6 +212,7 @@ void worker_main(lrb_queue* q) {
                 }
             }
             if (e != cudaSuccess) q->worker_error = cudaGetErrorString(e);
+            if (wait_expired) q->worker_error = "a bounded device wait expired in a split-precision wave";
             s.reqs.clear();
             s.busy = false;
             q->t_last = now;
@@ -198,13 +236,15 @@ void worker_main(lrb_queue* q) {
             q->reserved += wave_bytes;
             q->peak_reserved = std::max(q->peak_reserved, q->reserved);
             for (Request* r : s.reqs) r->state = kRunning;
+            const int precision = q->precision;
+            s.split = precision >= LRB_PREC_SPLIT_BF16_S3;
             s.busy = true;
             ++busy;
             q->max_concurrent_waves = std::max<uint64_t>(q->max_concurrent_waves, busy);
             ++q->waves;
             q->wave_entries += entries;
             lk.unlock();
-            const lrb_status st = launch_wave(q, s);
+            const lrb_status st = launch_wave(q, s, precision);
             lk.lock();
             if (st != LRB_OK) {
                 for (Request* r : s.reqs) {
@@ -253,10 +293,12 @@ lrb_status lrb_queue_create(lrb_handle* h, size_t hbm_budget_bytes, int max_infl
     q->slots.resize(max_inflight);
     for (Slot& s : q->slots) {
         if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMallocHost((void**)&s.h_status, sizeof(int)) != cudaSuccess) {
             for (Slot& t : q->slots) {
                 if (t.done) cudaEventDestroy(t.done);
                 if (t.stream) cudaStreamDestroy(t.stream);
+                if (t.h_status) cudaFreeHost(t.h_status);
             }
             delete q;
             return qfail(LRB_ERR_DEVICE, "stream/event creation");
@@ -272,6 +314,16 @@ lrb_status lrb_queue_set_limits(lrb_queue* q, size_t max_waiting, size_t max_wav
     std::lock_guard<std::mutex> lk(q->mu);
     q->max_waiting = max_waiting;
     q->max_wave_entries = max_wave_entries;
+    return LRB_OK;
+}
+
+lrb_status lrb_queue_set_precision(lrb_queue* q, int32_t precision) {
+    if (!q) return qfail(LRB_ERR_INVALID, "NULL queue");
+    if (precision != LRB_PREC_FP64 && precision != LRB_PREC_FP64_DMMA_ALLOWED &&
+        (precision < LRB_PREC_SPLIT_BF16_S3 || precision > LRB_PREC_SPLIT_FP16_S4))
+        return qfail(LRB_ERR_INVALID, "unknown precision");
+    std::lock_guard<std::mutex> lk(q->mu);
+    q->precision = precision;
     return LRB_OK;
 }
 
@@ -417,6 +469,7 @@ lrb_status lrb_queue_destroy(lrb_queue* q, int timeout_ms) {
         }
         cudaEventDestroy(s.done);
         cudaStreamDestroy(s.stream);
+        if (!q->abandon) cudaFreeHost(s.h_status);
     }
     for (auto& kv : q->reqs) delete kv.second;
     delete q;

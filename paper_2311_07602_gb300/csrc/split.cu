@@ -529,6 +529,19 @@ struct SplitPlan {
     int n_items = 0;
 };
 
+void build_items(const lrb_gemm_desc* descs, size_t count, std::vector<int4>& items) {
+    items.clear();
+    for (size_t e = 0; e < count; ++e)
+        for (int c0 = 0; c0 < descs[e].n; c0 += kTN)
+            for (int r0 = 0; r0 < descs[e].m; r0 += kTM) items.push_back(make_int4((int)e, r0, c0, 0));
+}
+
+cudaError_t launch_raw(int precision, const DevDesc* d_descs, const int4* d_items, int n_items, int* d_status,
+                       cudaStream_t s) {
+    static_assert(sizeof(int4) == sizeof(SItem), "tile layout");
+    return launch_prec(precision, d_descs, reinterpret_cast<const SItem*>(d_items), n_items, d_status, nullptr, 0, s);
+}
+
 int chunk_len(int precision) {
     return (precision == LRB_PREC_SPLIT_FP16_S3 || precision == LRB_PREC_SPLIT_FP16_S4) ? 32 : 64;
 }

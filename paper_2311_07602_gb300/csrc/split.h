@@ -1,8 +1,10 @@
 // Split-precision (Ozaki-style) path: internal interface used by the C ABI.
 #pragma once
 #include <cstddef>
+#include <vector>
 #include <cuda_runtime.h>
 #include "../../include/lrbatch.h"
+#include "lrb_internal.h"
 
 namespace lrb {
 namespace split {
@@ -19,6 +21,12 @@ cudaError_t launch(SplitPlan* p, cudaStream_t s);
 cudaError_t launch_dump(SplitPlan* p, float* dump, cudaStream_t s);
 // Reads the plan's device status word (1 after a bounded wait expired).
 int read_status(SplitPlan* p, cudaStream_t s, int* value);
+// Tile list (int4 per 128 x 64 output tile: entry, row0, col0, 0) of a batch
+// and the launch of the split kernel on uploaded descriptors / tiles (used by
+// the serving queue, whose waves live in stream-slot memory).
+void build_items(const lrb_gemm_desc* descs, size_t count, std::vector<int4>& items);
+cudaError_t launch_raw(int precision, const DevDesc* d_descs, const int4* d_items, int n_items, int* d_status,
+                       cudaStream_t s);
 int chunk_len(int precision);
 int digit_count(int precision);
 void destroy(SplitPlan* p);

@@ -93,6 +93,7 @@ def lib():
             "lrb_lr_plan_create": ([vp, vp, sz, i32, ctypes.POINTER(vp)], i32),
             "lrb_queue_create": ([vp, sz, ctypes.c_int, ctypes.POINTER(vp)], i32),
             "lrb_queue_set_limits": ([vp, sz, sz], i32),
+            "lrb_queue_set_precision": ([vp, i32], i32),
             "lrb_queue_submit": ([vp, vp, sz, ctypes.POINTER(ctypes.c_uint64)], i32),
             "lrb_queue_poll": ([vp, ctypes.c_uint64], i32),
             "lrb_queue_wait": ([vp, ctypes.c_uint64, ctypes.c_int], i32),
@@ -297,6 +298,9 @@ class Queue:
 
     def set_limits(self, max_waiting: int, max_wave_entries: int = 1 << 16):
         check(lib().lrb_queue_set_limits(self.ptr, max_waiting, max_wave_entries))
+
+    def set_precision(self, precision: int):
+        check(lib().lrb_queue_set_precision(self.ptr, precision))
 
     def submit(self, descs: np.ndarray):
         """Returns (status, ticket); status is LRB_OK, LRB_ERR_BUDGET, LRB_ERR_QUEUE_FULL or LRB_ERR_INVALID."""

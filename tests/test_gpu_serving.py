@@ -114,3 +114,42 @@ def test_queue_full_and_bounded_waits(handle):
         assert q.latency(tb) > 0
         assert q.poll(123456789) == L.LRB_ERR_INVALID
     del big, tiny
+
+
+def test_split_precision_waves_alone_equals_mix(handle):
+    """Waves in BF16 S=3 split precision: each request's result is bitwise the
+    same alone and in a mix, and matches the split oracle within the binary64
+    regrouping bound."""
+    import oracle
+    from oracle import PRESETS
+    from tests.parity import entry_view
+    batch, reqs = requests(10, seed=53, max_products=5, bmax=400)
+    Ah, Bh, C0 = host(batch.A), host(batch.B), host(batch.C)
+    outs = []
+    for slots, wave_entries in ((1, 1 << 16), (4, 6)):
+        dev = batch.to("cuda")
+        d = L.descs_for(dev)
+        with L.Queue(handle, budget_bytes=40 << 30, max_inflight=slots) as q:
+            q.set_precision(L.LRB_PREC_SPLIT_BF16_S3)
+            q.set_limits(4096, max_wave_entries=wave_entries)
+            tickets = []
+            for lo, hi in reqs:
+                st, t = q.submit(d[lo:hi])
+                assert st == L.LRB_OK
+                tickets.append(t)
+                if slots == 1:
+                    assert q.wait(t, 60000) == L.LRB_OK
+            for t in tickets:
+                assert q.wait(t, 60000) == L.LRB_OK
+        outs.append(host(dev.C))
+    assert np.array_equal(outs[0].view(np.uint64), outs[1].view(np.uint64))
+    p = PRESETS["bf16_s3"]
+    for e in range(len(batch)):
+        m, n, k = int(batch.m[e]), int(batch.n[e]), int(batch.k[e])
+        A = entry_view(Ah, int(batch.offA[e]), m, k, int(batch.lda[e])).copy()
+        B = entry_view(Bh, int(batch.offB[e]), k, n, int(batch.ldb[e])).copy()
+        C = entry_view(C0, int(batch.offC[e]), m, n, int(batch.ldc[e])).copy()
+        exp = oracle.split_gemm(A, B, C, p)
+        got = entry_view(outs[1], int(batch.offC[e]), m, n, int(batch.ldc[e]))
+        nadd = ((k + p.kc - 1) // p.kc) * (len(p.levels()) + 1)
+        assert np.all(np.abs(got - exp) <= 2 * oracle.gamma(nadd) * oracle.recombination_magnitude(A, B, C, p))
