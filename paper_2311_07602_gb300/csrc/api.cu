@@ -191,6 +191,16 @@ int heuristic_variant(int m, int n, int k, bool dmma_ok) {
 
 }  // namespace
 
+namespace {
+// One host<->device copy of lrb_execute_host: a 2-D block, or a merged 1-D run.
+struct HostCopy {
+    const double* host;
+    size_t dev;        // element offset in the arena
+    int rows, cols, ld;
+    size_t elems;      // contiguous run length (tight blocks)
+};
+}  // namespace
+
 struct lrb_handle {
     int device = 0;
     int sms = 0;
@@ -208,6 +218,10 @@ struct lrb_handle {
     size_t arena_bytes = 0;
     std::vector<lrb_gemm_desc> host_key;
     std::vector<size_t> host_cut;
+    // the caller's last host descriptor array and its copy lists: a repeated
+    // batch skips validation, layout and planning
+    std::vector<lrb_gemm_desc> host_in;
+    std::vector<std::vector<HostCopy>> host_h2d, host_d2h;
     lrb_plan_opts host_opts{};
     std::vector<lrb_plan*> host_plans;
     cudaStream_t copy_in = nullptr, copy_out = nullptr;
@@ -724,145 +738,155 @@ lrb_status lrb_execute_host(lrb_handle* h, const lrb_gemm_desc* host_descs, size
                             void* stream) {
     if (!h) return fail(LRB_ERR_INVALID, "handle is NULL");
     const lrb_plan_opts o = opts ? *opts : default_opts();
-    lrb_status st = validate(host_descs, count, o);
-    if (st != LRB_OK) return st;
+    if (!host_descs || count == 0) return validate(host_descs, count, o);
+    lrb_status st = LRB_OK;
     LRB_CUDA(cudaSetDevice(h->device));
     cudaStream_t s = (cudaStream_t)stream;
 
-    // Pieces: contiguous entry ranges of about equal bytes (at most 8, at
-    // least 64 MB each).  Piece p's copies in, its launch and its copies out
-    // run on three streams joined by events, so piece p+1 moves in while p
-    // computes and p-1 moves out.
-    std::vector<double> eb(count);
-    double total = 0;
-    for (size_t e = 0; e < count; ++e) {
-        const lrb_gemm_desc& x = host_descs[e];
-        eb[e] = 8.0 * ((double)x.m * x.k + (double)x.k * x.n + 2.0 * x.m * x.n);
-        total += eb[e];
-    }
-    const int npieces = (int)std::max(1.0, std::min(8.0, std::floor(total / (64.0 * (1 << 20)))));
-    std::vector<size_t> cut(1, 0);
-    {
-        double acc = 0;
+    const bool cached = !h->host_plans.empty() && h->host_in.size() == count &&
+                        std::memcmp(h->host_in.data(), host_descs, sizeof(lrb_gemm_desc) * count) == 0 &&
+                        std::memcmp(&h->host_opts, &o, sizeof(o)) == 0;
+    if (!cached) {
+        st = validate(host_descs, count, o);
+        if (st != LRB_OK) return st;
+        // Pieces: contiguous entry ranges of about equal bytes (at most 16, at
+        // least 64 MB each).  Piece p's copies in, its launch and its copies out
+        // run on three streams joined by events, so piece p+1 moves in while p
+        // computes and p-1 moves out.
+        std::vector<double> eb(count);
+        double total = 0;
         for (size_t e = 0; e < count; ++e) {
-            acc += eb[e];
-            if ((int)cut.size() < npieces && acc >= total * (double)cut.size() / npieces && e + 1 < count)
-                cut.push_back(e + 1);
+            const lrb_gemm_desc& x = host_descs[e];
+            eb[e] = 8.0 * ((double)x.m * x.k + (double)x.k * x.n + 2.0 * x.m * x.n);
+            total += eb[e];
         }
-        cut.push_back(count);
-    }
-    const int P = (int)cut.size() - 1;
+        const int npieces = (int)std::max(1.0, std::min(16.0, std::floor(total / (64.0 * (1 << 20)))));
+        std::vector<size_t> cut(1, 0);
+        {
+            double acc = 0;
+            for (size_t e = 0; e < count; ++e) {
+                acc += eb[e];
+                if ((int)cut.size() < npieces && acc >= total * (double)cut.size() / npieces && e + 1 < count)
+                    cut.push_back(e + 1);
+            }
+            cut.push_back(count);
+        }
+        const int P = (int)cut.size() - 1;
 
-    // Device layout: piece by piece, A blocks then B blocks then C blocks,
-    // each packed with ld = rows.  An A or B block whose (pointer, rows,
-    // cols, ld) repeats an earlier one is shared (copied by the first piece).
-    struct Copy {
-        const double* host;
-        size_t dev;        // element offset in the arena
-        int rows, cols, ld;
-        size_t elems;      // contiguous run length (tight blocks)
-    };
-    std::vector<lrb_gemm_desc> dd(host_descs, host_descs + count);
-    std::vector<std::vector<Copy>> h2d(P), d2h(P);
-    std::vector<size_t> wa(count), wb(count), wc(count);
-    std::map<std::tuple<uintptr_t, int, int, int>, size_t> seen;
-    size_t cursor = 0;
-    for (int pc = 0; pc < P; ++pc) {
-        for (int cls = 0; cls < 3; ++cls) {
-            std::vector<Copy>& list = h2d[pc];
-            const size_t cls_start = list.size();   // runs never merge across operand classes
-            for (size_t e = cut[pc]; e < cut[pc + 1]; ++e) {
-                const lrb_gemm_desc& x = host_descs[e];
-                const double* ptr = cls == 0 ? x.A : cls == 1 ? x.B : x.C;
-                const int rows = cls == 0 ? x.m : cls == 1 ? x.k : x.m;
-                const int cols = cls == 0 ? x.k : cls == 1 ? x.n : x.n;
-                const int ld = cls == 0 ? x.lda : cls == 1 ? x.ldb : x.ldc;
-                std::vector<size_t>& where = cls == 0 ? wa : cls == 1 ? wb : wc;
-                if (cls < 2) {
-                    auto it = seen.find(std::make_tuple((uintptr_t)ptr, rows, cols, ld));
-                    if (it != seen.end()) {
-                        where[e] = it->second;
-                        continue;
+        // Device layout: piece by piece, A blocks then B blocks then C blocks,
+        // each packed with ld = rows.  An A or B block whose (pointer, rows,
+        // cols, ld) repeats an earlier one is shared (copied by the first piece).
+        using Copy = HostCopy;
+        std::vector<lrb_gemm_desc> dd(host_descs, host_descs + count);
+        std::vector<std::vector<Copy>> h2d(P), d2h(P);
+        std::vector<size_t> wa(count), wb(count), wc(count);
+        std::map<std::tuple<uintptr_t, int, int, int>, size_t> seen;
+        size_t cursor = 0;
+        for (int pc = 0; pc < P; ++pc) {
+            for (int cls = 0; cls < 3; ++cls) {
+                std::vector<Copy>& list = h2d[pc];
+                const size_t cls_start = list.size();   // runs never merge across operand classes
+                for (size_t e = cut[pc]; e < cut[pc + 1]; ++e) {
+                    const lrb_gemm_desc& x = host_descs[e];
+                    const double* ptr = cls == 0 ? x.A : cls == 1 ? x.B : x.C;
+                    const int rows = cls == 0 ? x.m : cls == 1 ? x.k : x.m;
+                    const int cols = cls == 0 ? x.k : cls == 1 ? x.n : x.n;
+                    const int ld = cls == 0 ? x.lda : cls == 1 ? x.ldb : x.ldc;
+                    std::vector<size_t>& where = cls == 0 ? wa : cls == 1 ? wb : wc;
+                    if (cls < 2) {
+                        auto it = seen.find(std::make_tuple((uintptr_t)ptr, rows, cols, ld));
+                        if (it != seen.end()) {
+                            where[e] = it->second;
+                            continue;
+                        }
+                        seen[std::make_tuple((uintptr_t)ptr, rows, cols, ld)] = cursor;
                     }
-                    seen[std::make_tuple((uintptr_t)ptr, rows, cols, ld)] = cursor;
-                }
-                const size_t elems = (size_t)rows * cols;
-                where[e] = cursor;
-                Copy c{ptr, cursor, rows, cols, ld, elems};
-                if (list.size() > cls_start && ld == rows) {
-                    Copy& b = list.back();
-                    if (b.ld == b.rows && b.host + b.elems == ptr && b.dev + b.elems == cursor) {
-                        b.elems += elems;
-                        b.cols = -1;   // merged run: a 1-D copy
+                    const size_t elems = (size_t)rows * cols;
+                    where[e] = cursor;
+                    Copy c{ptr, cursor, rows, cols, ld, elems};
+                    if (list.size() > cls_start && ld == rows) {
+                        Copy& b = list.back();
+                        if (b.ld == b.rows && b.host + b.elems == ptr && b.dev + b.elems == cursor) {
+                            b.elems += elems;
+                            b.cols = -1;   // merged run: a 1-D copy
+                        } else {
+                            list.push_back(c);
+                        }
                     } else {
                         list.push_back(c);
                     }
-                } else {
-                    list.push_back(c);
+                    cursor += elems;
                 }
-                cursor += elems;
+                if (cls == 2) d2h[pc].assign(list.begin() + cls_start, list.end());
             }
-            if (cls == 2) d2h[pc].assign(list.begin() + cls_start, list.end());
         }
-    }
 
-    const size_t need = cursor * 8 + 256;
-    if (need > h->arena_bytes) {
-        for (lrb_plan* p : h->host_plans) free_plan(p);
-        h->host_plans.clear();
-        cudaStreamSynchronize(s);
-        if (h->arena) cudaFree(h->arena);
-        h->arena = nullptr;
-        h->arena_bytes = 0;
-        cudaError_t ce = cudaMalloc(&h->arena, need);
-        if (ce != cudaSuccess) return fail(LRB_ERR_NOMEM, std::string("host-run arena: ") + cudaGetErrorString(ce));
-        h->arena_bytes = need;
-        h->host_key.clear();
-    }
-    if (!h->copy_in) {
-        LRB_CUDA(cudaStreamCreateWithFlags(&h->copy_in, cudaStreamNonBlocking));
-        LRB_CUDA(cudaStreamCreateWithFlags(&h->copy_out, cudaStreamNonBlocking));
-    }
-    while ((int)h->ev_in.size() < P) {
-        cudaEvent_t a, b;
-        LRB_CUDA(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
-        LRB_CUDA(cudaEventCreateWithFlags(&b, cudaEventDisableTiming));
-        h->ev_in.push_back(a);
-        h->ev_done.push_back(b);
-    }
-    double* base = (double*)h->arena;
-    for (size_t e = 0; e < count; ++e) {
-        dd[e].A = base + wa[e];
-        dd[e].B = base + wb[e];
-        dd[e].C = base + wc[e];
-        dd[e].lda = dd[e].m;
-        dd[e].ldb = dd[e].k;
-        dd[e].ldc = dd[e].m;
-    }
-    const bool same = !h->host_plans.empty() && h->host_key.size() == count && h->host_cut == cut &&
-                      std::memcmp(h->host_key.data(), dd.data(), sizeof(lrb_gemm_desc) * count) == 0 &&
-                      std::memcmp(&h->host_opts, &o, sizeof(o)) == 0;
-    if (!same) {
-        cudaStreamSynchronize(s);
-        for (lrb_plan* p : h->host_plans) free_plan(p);
-        h->host_plans.clear();
-        for (int pc = 0; pc < P; ++pc) {
-            lrb_plan* p = nullptr;
-            lrb_plan_opts po = o;
-            po.check_alias = 0;   // checked above on the caller's host ranges
-            st = lrb_plan_create(h, dd.data() + cut[pc], cut[pc + 1] - cut[pc], &po, &p);
-            if (st != LRB_OK) {
-                for (lrb_plan* q : h->host_plans) free_plan(q);
-                h->host_plans.clear();
-                return st;
-            }
-            h->host_plans.push_back(p);
+        const size_t need = cursor * 8 + 256;
+        if (need > h->arena_bytes) {
+            for (lrb_plan* p : h->host_plans) free_plan(p);
+            h->host_plans.clear();
+            cudaStreamSynchronize(s);
+            if (h->arena) cudaFree(h->arena);
+            h->arena = nullptr;
+            h->arena_bytes = 0;
+            cudaError_t ce = cudaMalloc(&h->arena, need);
+            if (ce != cudaSuccess) return fail(LRB_ERR_NOMEM, std::string("host-run arena: ") + cudaGetErrorString(ce));
+            h->arena_bytes = need;
+            h->host_key.clear();
         }
-        h->host_key = dd;
-        h->host_cut = cut;
-        h->host_opts = o;
+        if (!h->copy_in) {
+            LRB_CUDA(cudaStreamCreateWithFlags(&h->copy_in, cudaStreamNonBlocking));
+            LRB_CUDA(cudaStreamCreateWithFlags(&h->copy_out, cudaStreamNonBlocking));
+        }
+        while ((int)h->ev_in.size() < P) {
+            cudaEvent_t a, b;
+            LRB_CUDA(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+            LRB_CUDA(cudaEventCreateWithFlags(&b, cudaEventDisableTiming));
+            h->ev_in.push_back(a);
+            h->ev_done.push_back(b);
+        }
+        double* base = (double*)h->arena;
+        for (size_t e = 0; e < count; ++e) {
+            dd[e].A = base + wa[e];
+            dd[e].B = base + wb[e];
+            dd[e].C = base + wc[e];
+            dd[e].lda = dd[e].m;
+            dd[e].ldb = dd[e].k;
+            dd[e].ldc = dd[e].m;
+        }
+        const bool same = !h->host_plans.empty() && h->host_key.size() == count && h->host_cut == cut &&
+                          std::memcmp(h->host_key.data(), dd.data(), sizeof(lrb_gemm_desc) * count) == 0 &&
+                          std::memcmp(&h->host_opts, &o, sizeof(o)) == 0;
+        if (!same) {
+            cudaStreamSynchronize(s);
+            for (lrb_plan* p : h->host_plans) free_plan(p);
+            h->host_plans.clear();
+            for (int pc = 0; pc < P; ++pc) {
+                lrb_plan* p = nullptr;
+                lrb_plan_opts po = o;
+                po.check_alias = 0;   // checked above on the caller's host ranges
+                st = lrb_plan_create(h, dd.data() + cut[pc], cut[pc + 1] - cut[pc], &po, &p);
+                if (st != LRB_OK) {
+                    for (lrb_plan* q : h->host_plans) free_plan(q);
+                    h->host_plans.clear();
+                    return st;
+                }
+                h->host_plans.push_back(p);
+            }
+            h->host_key = dd;
+            h->host_cut = cut;
+            h->host_opts = o;
+        }
+
+        h->host_in.assign(host_descs, host_descs + count);
+        h->host_h2d = h2d;
+        h->host_d2h = d2h;
     }
-    auto copy = [&](const Copy& c, bool to_dev, cudaStream_t cs) -> cudaError_t {
+    const int P = (int)h->host_h2d.size();
+    const std::vector<std::vector<HostCopy>>& h2d = h->host_h2d;
+    const std::vector<std::vector<HostCopy>>& d2h = h->host_d2h;
+    double* base = (double*)h->arena;
+    auto copy = [&](const HostCopy& c, bool to_dev, cudaStream_t cs) -> cudaError_t {
         double* dptr = base + c.dev;
         if (c.cols < 0 || c.ld == c.rows) {
             const size_t bytes = c.elems * 8;
@@ -878,7 +902,7 @@ lrb_status lrb_execute_host(lrb_handle* h, const lrb_gemm_desc* host_descs, size
     LRB_CUDA(cudaEventRecord(h->ev_done[0], s));
     LRB_CUDA(cudaStreamWaitEvent(h->copy_in, h->ev_done[0], 0));
     for (int pc = 0; pc < P; ++pc) {
-        for (const Copy& c : h2d[pc]) LRB_CUDA(copy(c, true, h->copy_in));
+        for (const HostCopy& c : h2d[pc]) LRB_CUDA(copy(c, true, h->copy_in));
         LRB_CUDA(cudaEventRecord(h->ev_in[pc], h->copy_in));
     }
     for (int pc = 0; pc < P; ++pc) {
@@ -887,7 +911,7 @@ lrb_status lrb_execute_host(lrb_handle* h, const lrb_gemm_desc* host_descs, size
         if (st != LRB_OK) return st;
         LRB_CUDA(cudaEventRecord(h->ev_done[pc], s));
         LRB_CUDA(cudaStreamWaitEvent(h->copy_out, h->ev_done[pc], 0));
-        for (const Copy& c : d2h[pc]) LRB_CUDA(copy(c, false, h->copy_out));
+        for (const HostCopy& c : d2h[pc]) LRB_CUDA(copy(c, false, h->copy_out));
     }
     LRB_CUDA(cudaStreamSynchronize(h->copy_out));
     LRB_CUDA(cudaStreamSynchronize(s));

@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
                 long long I = 0;
 #pragma unroll
                 for (int l = 0; l < S; ++l)   // level L = l + 2, weight 2^(beta (S - 1 - l))
-                    I = (I << BETA) + (long long)__float2int_rn(__uint_as_float(v[l][jj]));
+                    I = I * (1ll << BETA) + (long long)__float2int_rn(__uint_as_float(v[l][jj]));
                 if (dump != nullptr && row < prev.d.m && prev.col0 + j < prev.d.n) {
 #pragma unroll
                     for (int l = 0; l < S; ++l)
@@ -326,10 +326,14 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
             uint8_t* planeB = planeA + S * C_::planeA;
             // (1) loads: A row `row`, chunk columns [q QC, q QC + QC); B columns 4 w .. 4 w + 3
             double av[QC];
+            {
+                const double* ap = d.A + (size_t)row + (size_t)(k0 + q * QC) * (size_t)d.lda;
+                const int ncol = row_ok ? min(QC, kcl - q * QC) : 0;   // valid columns of this quarter
 #pragma unroll
-            for (int p = 0; p < QC; ++p) {
-                const int col = q * QC + p;
-                av[p] = (row_ok && col < kcl) ? __ldg(d.A + (size_t)row + (size_t)(k0 + col) * (size_t)d.lda) : 0.0;
+                for (int p = 0; p < QC; ++p) {
+                    av[p] = p < ncol ? __ldg(ap) : 0.0;
+                    ap += d.lda;
+                }
             }
             double bv[4][KB];
 #pragma unroll
