@@ -204,8 +204,9 @@ struct HostCopy {
 struct lrb_handle {
     int device = 0;
     int sms = 0;
-    int blocks_per_sm = 0;        // narrow persistent kernel
-    int blocks_per_sm_wide = 0;   // wide persistent kernel
+    int blocks_per_sm = 0;        // narrow persistent kernel (variant set 1)
+    int blocks_per_sm_wide = 0;   // wide persistent kernel (set 2)
+    int blocks_per_sm_slim = 0;   // slim persistent kernel (set 0)
     std::string gpu_key;
     std::string cache_path;
     std::map<std::string, int> tuned;
@@ -224,8 +225,9 @@ struct lrb_handle {
     std::vector<std::vector<HostCopy>> host_h2d, host_d2h;
     lrb_plan_opts host_opts{};
     std::vector<lrb_plan*> host_plans;
-    cudaStream_t copy_in = nullptr, copy_out = nullptr;
+    cudaStream_t copy_in = nullptr, copy_out = nullptr, compute2 = nullptr;
     std::vector<cudaEvent_t> ev_in, ev_done;
+    cudaEvent_t ev_join = nullptr;
 };
 
 struct lrb_plan {
@@ -239,7 +241,7 @@ struct lrb_plan {
     int* d_head = nullptr;
     int n_items = 0;
     int grid = 0;
-    bool wide = false;   // some tile needs the wide persistent kernel
+    int set = 0;         // variant set of the persistent kernel (largest set of any tile)
     std::vector<Group> groups;
     bool use_graph = false;
     cudaGraph_t graph = nullptr;
@@ -349,7 +351,7 @@ lrb_status tune_bucket(lrb_handle* h, int m, int n, int k, bool dmma_ok, int* be
     *best = heuristic_variant(m, n, k, dmma_ok);
     for (int v = 0; v < kNumVariants; ++v) {
         const Variant& V = kVariants[v];
-        if (!variant_is_narrow(v)) continue;   // tuned plans keep the 4-CTA persistent kernel
+        if (variant_set(v) != 0) continue;   // tuned plans run in the slim persistent kernel (5 CTAs/SM)
         if (V.dmma && !dmma_ok) continue;
         // skip tiles more than twice as tall/wide as the shape needs
         if (V.bm() > 32 && V.bm() >= 2 * std::max(M, 32)) continue;
@@ -454,7 +456,7 @@ void lrb::plan_tiles(const lrb_gemm_desc* d, size_t count, const std::vector<int
     make_tiles(d, count, var, items);
 }
 lrb::HandleInfo lrb::handle_info(const lrb_handle* h) {
-    return HandleInfo{h->device, h->sms, h->blocks_per_sm, h->blocks_per_sm_wide};
+    return HandleInfo{h->device, h->sms, h->blocks_per_sm, h->blocks_per_sm_wide, h->blocks_per_sm_slim};
 }
 lrb_plan_opts lrb::default_plan_opts() { return default_opts(); }
 
@@ -521,9 +523,10 @@ lrb_status lrb_create(lrb_handle** out, int device) {
         return cuda_fail(e, "cudaGetDeviceProperties");
     }
     h->sms = prop.multiProcessorCount;
-    h->blocks_per_sm = persistent_blocks_per_sm(false);
-    h->blocks_per_sm_wide = persistent_blocks_per_sm(true);
-    if (h->blocks_per_sm <= 0 || h->blocks_per_sm_wide <= 0) {
+    h->blocks_per_sm = persistent_blocks_per_sm(1);
+    h->blocks_per_sm_wide = persistent_blocks_per_sm(2);
+    h->blocks_per_sm_slim = persistent_blocks_per_sm(0);
+    if (h->blocks_per_sm <= 0 || h->blocks_per_sm_wide <= 0 || h->blocks_per_sm_slim <= 0) {
         delete h;
         return fail(LRB_ERR_DEVICE, "persistent kernel does not fit on this device");
     }
@@ -552,6 +555,8 @@ lrb_status lrb_destroy(lrb_handle* h) {
     for (cudaEvent_t e : h->ev_done) cudaEventDestroy(e);
     if (h->copy_in) cudaStreamDestroy(h->copy_in);
     if (h->copy_out) cudaStreamDestroy(h->copy_out);
+    if (h->compute2) cudaStreamDestroy(h->compute2);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->arena) cudaFree(h->arena);
     if (h->scratch) cudaFree(h->scratch);
     if (h->stream) cudaStreamDestroy(h->stream);
@@ -661,9 +666,9 @@ lrb_status lrb_plan_create(lrb_handle* h, const lrb_gemm_desc* host_descs, size_
         free_plan(p);
         return cuda_fail(ce, "plan upload");
     }
-    for (size_t e = 0; e < count; ++e)
-        if (!variant_is_narrow(var[e])) p->wide = true;
-    p->grid = std::max(1, std::min(h->sms * (p->wide ? h->blocks_per_sm_wide : h->blocks_per_sm), p->n_items));
+    for (size_t e = 0; e < count; ++e) p->set = std::max(p->set, variant_set(var[e]));
+    const int per_sm = p->set == 0 ? h->blocks_per_sm_slim : p->set == 1 ? h->blocks_per_sm : h->blocks_per_sm_wide;
+    p->grid = std::max(1, std::min(h->sms * per_sm, p->n_items));
     p->info.items = p->n_items;
     p->info.dmma_items = 0;
     for (const Item& it : items) p->info.dmma_items += kVariants[it.variant].dmma ? 1 : 0;
@@ -674,7 +679,7 @@ lrb_status lrb_plan_create(lrb_handle* h, const lrb_gemm_desc* host_descs, size_
         cudaStream_t cs = h->stream;
         ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (ce == cudaSuccess) {
-            cudaError_t le = launch_persistent(p->d_descs, p->d_items, p->n_items, p->d_head, p->grid, cs, p->wide);
+            cudaError_t le = launch_persistent(p->d_descs, p->d_items, p->n_items, p->d_head, p->grid, cs, p->set);
             ce = cudaStreamEndCapture(cs, &p->graph);
             if (le != cudaSuccess) ce = le;
         }
@@ -713,7 +718,7 @@ lrb_status lrb_launch(lrb_plan* p, void* stream) {
         return LRB_OK;
     }
     cudaError_t e = p->use_graph ? cudaGraphLaunch(p->exec, s)
-                                 : launch_persistent(p->d_descs, p->d_items, p->n_items, p->d_head, p->grid, s, p->wide);
+                                 : launch_persistent(p->d_descs, p->d_items, p->n_items, p->d_head, p->grid, s, p->set);
     if (e != cudaSuccess) return cuda_fail(e, "persistent launch");
     return LRB_OK;
 }
@@ -837,6 +842,8 @@ lrb_status lrb_execute_host(lrb_handle* h, const lrb_gemm_desc* host_descs, size
         if (!h->copy_in) {
             LRB_CUDA(cudaStreamCreateWithFlags(&h->copy_in, cudaStreamNonBlocking));
             LRB_CUDA(cudaStreamCreateWithFlags(&h->copy_out, cudaStreamNonBlocking));
+            LRB_CUDA(cudaStreamCreateWithFlags(&h->compute2, cudaStreamNonBlocking));
+            LRB_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
         }
         while ((int)h->ev_in.size() < P) {
             cudaEvent_t a, b;
@@ -905,14 +912,21 @@ lrb_status lrb_execute_host(lrb_handle* h, const lrb_gemm_desc* host_descs, size
         for (const HostCopy& c : h2d[pc]) LRB_CUDA(copy(c, true, h->copy_in));
         LRB_CUDA(cudaEventRecord(h->ev_in[pc], h->copy_in));
     }
+    // pieces alternate between the caller's stream and a second compute
+    // stream, so one piece's last tiles overlap the next piece's first ones
+    LRB_CUDA(cudaStreamWaitEvent(h->compute2, h->ev_done[0], 0));
     for (int pc = 0; pc < P; ++pc) {
-        LRB_CUDA(cudaStreamWaitEvent(s, h->ev_in[pc], 0));
-        st = lrb_launch(h->host_plans[pc], stream);
+        cudaStream_t cs = (pc & 1) ? h->compute2 : s;
+        LRB_CUDA(cudaStreamWaitEvent(cs, h->ev_in[pc], 0));
+        st = lrb_launch(h->host_plans[pc], (void*)cs);
         if (st != LRB_OK) return st;
-        LRB_CUDA(cudaEventRecord(h->ev_done[pc], s));
+        LRB_CUDA(cudaEventRecord(h->ev_done[pc], cs));
         LRB_CUDA(cudaStreamWaitEvent(h->copy_out, h->ev_done[pc], 0));
         for (const HostCopy& c : d2h[pc]) LRB_CUDA(copy(c, false, h->copy_out));
     }
+    // the caller's stream ends after everything, as before
+    LRB_CUDA(cudaEventRecord(h->ev_join, h->copy_out));
+    LRB_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
     LRB_CUDA(cudaStreamSynchronize(h->copy_out));
     LRB_CUDA(cudaStreamSynchronize(s));
     return LRB_OK;

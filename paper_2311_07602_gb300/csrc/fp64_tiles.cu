@@ -288,21 +288,23 @@ __device__ __forceinline__ void tile_dmma(const DevDesc& d, int m0, int n0, doub
         }
 }
 
-// WIDE = false dispatches only the variants that fit 128 registers per
-// thread, so the narrow persistent kernel keeps 4 CTAs (16 warps) per SM.
-template <bool WIDE>
+// Variant sets of the persistent kernel: SET 0 (slim) holds the tiles that
+// fit 102 registers (5 CTAs = 20 warps per SM), SET 1 (narrow) adds the
+// 64x64 and 128x32 DFMA tiles (168 registers, 3 CTAs), SET 2 (wide) every
+// variant (1 CTA).
+template <int SET>
 __device__ __forceinline__ void run_tile(int variant, const DevDesc& d, int m0, int n0, double* smem) {
     switch (variant) {
         case 0: tile_dfma<2, 2, 4, 1>(d, m0, n0, smem); break;
         case 1: tile_dfma<2, 4, 4, 1>(d, m0, n0, smem); break;
         case 2: tile_dfma<2, 8, 4, 1>(d, m0, n0, smem); break;
-        case 3: tile_dfma<2, 16, 4, 1>(d, m0, n0, smem); break;
-        case 4: tile_dfma<4, 8, 4, 1>(d, m0, n0, smem); break;
-        case 5: if constexpr (WIDE) tile_dfma<4, 16, 4, 1>(d, m0, n0, smem); break;
+        case 3: if constexpr (SET >= 1) tile_dfma<2, 16, 4, 1>(d, m0, n0, smem); break;
+        case 4: if constexpr (SET >= 1) tile_dfma<4, 8, 4, 1>(d, m0, n0, smem); break;
+        case 5: if constexpr (SET >= 2) tile_dfma<4, 16, 4, 1>(d, m0, n0, smem); break;
         case 6: tile_dfma<1, 8, 1, 4>(d, m0, n0, smem); break;
         case 7: tile_dfma<1, 16, 2, 2>(d, m0, n0, smem); break;
         case 8: tile_dmma<4>(d, m0, n0, smem); break;
-        case 9: if constexpr (WIDE) tile_dmma<8>(d, m0, n0, smem); break;
+        case 9: if constexpr (SET >= 2) tile_dmma<8>(d, m0, n0, smem); break;
         default: break;   // planner never emits other ids
     }
 }
@@ -310,8 +312,8 @@ __device__ __forceinline__ void run_tile(int variant, const DevDesc& d, int m0, 
 // Persistent kernel: each CTA takes the next tile from the work counter until
 // the list (ordered longest-first by the planner) is exhausted.  No CTA ever
 // waits for another; the counter is the only shared state.
-template <bool WIDE>
-__global__ void __launch_bounds__(kThreads, WIDE ? 1 : 3) k_persistent(const DevDesc* __restrict__ descs,
+template <int SET>
+__global__ void __launch_bounds__(kThreads, SET == 0 ? 5 : SET == 1 ? 3 : 1) k_persistent(const DevDesc* __restrict__ descs,
                                                                       const Item* __restrict__ items, int n_items,
                                                                       int* __restrict__ head) {
     extern __shared__ __align__(16) double smem[];
@@ -324,7 +326,7 @@ __global__ void __launch_bounds__(kThreads, WIDE ? 1 : 3) k_persistent(const Dev
         const DevDesc d = descs[item.entry];
         __syncthreads();                                   // every thread has read s_item
         if (threadIdx.x == 0) s_item = atomicAdd(head, 1);  // claim the next tile while this one runs
-        run_tile<WIDE>(item.variant, d, item.row0, item.col0, smem);
+        run_tile<SET>(item.variant, d, item.row0, item.col0, smem);
         __syncthreads();
         it = s_item;
     }
@@ -343,7 +345,7 @@ __global__ void __launch_bounds__(kThreads) k_plain(const DevDesc* __restrict__ 
     const int bm = (V == 8 || V == 9) ? 64 : (V == 4 || V == 5 ? 128 : (V >= 6 ? 32 : 64));
     const int bn = V == 0 ? 8 : V == 1 ? 16 : V == 2 ? 32 : V == 3 ? 64 : V == 4 ? 32 : V == 5 ? 64
                  : V == 6 ? 8 : V == 7 ? 32 : V == 8 ? 32 : 64;
-    run_tile<true>(V, d, (t % tiles_m) * bm, (t / tiles_m) * bn, smem);
+    run_tile<2>(V, d, (t % tiles_m) * bm, (t / tiles_m) * bn, smem);
 }
 
 template <int V>
@@ -361,36 +363,45 @@ cudaError_t plain_launch(const DevDesc* d_descs, const int32_t* d_entries, int n
 
 }  // namespace
 
-bool variant_is_narrow(int v) { return v != 5 && v != 9; }
+int variant_set(int v) { return (v == 5 || v == 9) ? 2 : (v == 3 || v == 4) ? 1 : 0; }
 
-size_t persistent_smem_bytes(bool wide) {
+size_t persistent_smem_bytes(int set) {
     size_t m = 0;
     for (int v = 0; v < kNumVariants; ++v)
-        if (wide || variant_is_narrow(v)) m = std::max(m, variant_smem_bytes(v));
+        if (variant_set(v) <= set) m = std::max(m, variant_smem_bytes(v));
     return m;
 }
 
-int persistent_blocks_per_sm(bool wide) {
+namespace {
+template <int SET>
+int blocks_for() {
     int nb = 0;
-    const size_t smem = persistent_smem_bytes(wide);
-    auto kern = wide ? k_persistent<true> : k_persistent<false>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kThreads, smem) != cudaSuccess) return 0;
+    const size_t smem = persistent_smem_bytes(SET);
+    if (cudaFuncSetAttribute(k_persistent<SET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<SET>, kThreads, smem) != cudaSuccess) return 0;
     return nb;
+}
+}  // namespace
+
+int persistent_blocks_per_sm(int set) {
+    return set <= 0 ? blocks_for<0>() : set == 1 ? blocks_for<1>() : blocks_for<2>();
 }
 
 cudaError_t launch_persistent(const DevDesc* d_descs, const Item* d_items, int n_items, int* d_head, int grid,
-                              cudaStream_t s, bool wide) {
+                              cudaStream_t s, int set) {
     // the shared-memory attribute was set by persistent_blocks_per_sm() when
     // the handle was created (not here: this may run under stream capture)
-    const size_t smem = persistent_smem_bytes(wide);
+    const size_t smem = persistent_smem_bytes(set);
     cudaError_t e = cudaMemsetAsync(d_head, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     if (n_items <= 0) return cudaSuccess;
-    if (wide)
-        k_persistent<true><<<grid, kThreads, smem, s>>>(d_descs, d_items, n_items, d_head);
+    if (set <= 0)
+        k_persistent<0><<<grid, kThreads, smem, s>>>(d_descs, d_items, n_items, d_head);
+    else if (set == 1)
+        k_persistent<1><<<grid, kThreads, smem, s>>>(d_descs, d_items, n_items, d_head);
     else
-        k_persistent<false><<<grid, kThreads, smem, s>>>(d_descs, d_items, n_items, d_head);
+        k_persistent<2><<<grid, kThreads, smem, s>>>(d_descs, d_items, n_items, d_head);
     return cudaGetLastError();
 }
 

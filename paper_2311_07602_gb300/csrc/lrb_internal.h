@@ -61,14 +61,14 @@ size_t variant_smem_bytes(int v);
 size_t max_smem_bytes();
 
 // Kernel launchers (fp64_tiles.cu).
-// wide = false: the persistent kernel without the 128x64 DFMA and 64x64 DMMA
-// tiles (<= 128 registers, 4 CTAs per SM); wide = true: every variant.
+// set: the variant set of the persistent kernel (variant_set); 0 slim (5
+// CTAs per SM), 1 narrow (3 CTAs, the default), 2 wide (every variant).
 cudaError_t launch_persistent(const DevDesc* d_descs, const Item* d_items, int n_items,
-                              int* d_head, int grid, cudaStream_t s, bool wide = false);
+                              int* d_head, int grid, cudaStream_t s, int set = 1);
 cudaError_t launch_plain_group(int variant, const DevDesc* d_descs, const int32_t* d_entries,
                                int n_entries, int tiles_m, int tiles_n, cudaStream_t s);
-int persistent_blocks_per_sm(bool wide = false);
-bool variant_is_narrow(int v);
+int persistent_blocks_per_sm(int set = 1);
+int variant_set(int v);
 
 // Fused low-rank chain (lr_chain.cu).
 size_t lr_chain_smem_bytes();
@@ -81,7 +81,7 @@ void set_last_error(const char* msg);
 
 // Planner pieces (api.cu) used by the serving queue.
 struct HandleInfo {
-    int device, sms, blocks_per_sm, blocks_per_sm_wide;
+    int device, sms, blocks_per_sm, blocks_per_sm_wide, blocks_per_sm_slim;
 };
 HandleInfo handle_info(const lrb_handle* h);
 lrb_plan_opts default_plan_opts();

@@ -150,8 +150,8 @@ lrb_status launch_wave(lrb_queue* q, Slot& s, int precision) {
     if (st != LRB_OK) return st;
     std::vector<Item> items;
     plan_tiles(all.data(), all.size(), var, items);
-    bool wide = false;
-    for (int v : var) wide = wide || !variant_is_narrow(v);
+    int set = 0;
+    for (int v : var) set = std::max(set, variant_set(v));
     auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t o_items = align(sizeof(DevDesc) * all.size());
     const size_t o_head = o_items + align(sizeof(Item) * std::max<size_t>(items.size(), 1));
@@ -174,9 +174,9 @@ lrb_status launch_wave(lrb_queue* q, Slot& s, int precision) {
         e = cudaMemcpyAsync(d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice, s.stream);
     // pageable sources: the copies above are staged before they return, so
     // the host vectors may go out of scope
-    const int per_sm = wide ? q->hi.blocks_per_sm_wide : q->hi.blocks_per_sm;
+    const int per_sm = set == 0 ? q->hi.blocks_per_sm_slim : set == 1 ? q->hi.blocks_per_sm : q->hi.blocks_per_sm_wide;
     const int grid = std::max(1, std::min(q->hi.sms * per_sm, (int)items.size()));
-    if (e == cudaSuccess) e = launch_persistent(d_descs, d_items, (int)items.size(), d_head, grid, s.stream, wide);
+    if (e == cudaSuccess) e = launch_persistent(d_descs, d_items, (int)items.size(), d_head, grid, s.stream, set);
     if (e == cudaSuccess) e = cudaEventRecord(s.done, s.stream);
     return e == cudaSuccess ? LRB_OK : LRB_ERR_DEVICE;
 }
