@@ -9,6 +9,8 @@ library and does not import it.
   k, no fused multiply-add.
 * Split precision (split.py): the Ozaki-style digit splitting, exact int64
   digit products and binary64 recombination.
+* Low-rank producers and consumers (lowrank.py): randomized SVD of a dense
+  block, expansion U diag(S) V, rounded addition of two low-rank blocks.
 
 Arrays are numpy float64, column-major views described by (m, n, k, ld).
 """

@@ -150,3 +150,60 @@ def test_unmutated_split_oracle_passes():
 @pytest.mark.parametrize("name", sorted(SPLIT_MUTATIONS))
 def test_split_mutation_is_caught(name):
     assert not split_pins_pass(load_split_mutant(*SPLIT_MUTATIONS[name]))
+
+
+# Low-rank producer/consumer oracle (oracle/lowrank.py): an orthonormalisation
+# left out, B formed from A^T, the trailing instead of the leading triplets
+# kept, a power iteration without the transpose, the expansion without S, the
+# rounded addition without S or with its core transposed.
+LOWRANK_MUTATIONS = {
+    "no_orthonormalisation": ("    Q = orth(A @ Omega)\n", "    Q = A @ Omega\n"),
+    "B_from_A_transposed": ("    B = Q.T @ A\n", "    B = Q.T @ A.T\n"),
+    "trailing_triplets": ("return Q @ Ut[:, :r], sigma[:r].copy(), Wt[:r, :].copy()",
+                          "return Q @ Ut[:, -r:], sigma[-r:].copy(), Wt[-r:, :].copy()"),
+    "power_without_transpose": ("        Qt = orth(A.T @ Q)\n", "        Qt = orth(A @ Q)\n"),
+    "expand_unscaled": ("return D + (U * S[None, :]) @ V", "return D + U @ V"),
+    "round_add_unscaled": ("Uc = np.hstack([U1 * S1[None, :], U2 * S2[None, :]])", "Uc = np.hstack([U1, U2])"),
+    "round_add_core_transposed": ("np.linalg.svd(R1 @ R2.T)", "np.linalg.svd(R2 @ R1.T)"),
+}
+
+
+def load_lowrank_mutant(old, new) -> types.ModuleType:
+    src = open(os.path.join(ORACLE_DIR, "lowrank.py")).read()
+    assert src.count(old) == 1, old
+    mod = types.ModuleType("lowrank_mutant")
+    exec(compile(src.replace(old, new), "lowrank_mutant", "exec"), mod.__dict__)
+    return mod
+
+
+def lowrank_pins_pass(mod) -> bool:
+    """Run the low-rank pins (test_oracle_lowrank) against module `mod`."""
+    import importlib
+    T = importlib.import_module("test_oracle_lowrank")
+    cases = [(T.test_exact_rank_recovery, a) for a in [(60, 50, 5, 8, 0), (50, 80, 7, 7, 1), (33, 33, 1, 4, 0)]]
+    cases += [(T.test_known_spectrum_truncation, (q,)) for q in (0, 2)]
+    cases += [(T.test_range_finder_tail_bound, (q,)) for q in (0, 2)]
+    cases += [(f, ()) for f in (T.test_eckart_young_full_sampling, T.test_power_iteration_sharpens,
+                                T.test_orthonormal_factors, T.test_expand_integer_and_identity,
+                                T.test_round_add_known_spectrum, T.test_round_add_exact_and_cancellation)]
+    saved = T.L
+    T.L = mod
+    try:
+        for f, args in cases:
+            try:
+                f(*args)
+            except Exception:        # a failed assertion or a shape error: the pin caught it
+                return False
+    finally:
+        T.L = saved
+    return True
+
+
+def test_unmutated_lowrank_oracle_passes():
+    from oracle import lowrank
+    assert lowrank_pins_pass(lowrank)
+
+
+@pytest.mark.parametrize("name", sorted(LOWRANK_MUTATIONS))
+def test_lowrank_mutation_is_caught(name):
+    assert not lowrank_pins_pass(load_lowrank_mutant(*LOWRANK_MUTATIONS[name]))
