@@ -83,7 +83,11 @@ typedef struct lrb_plan_opts {
     int32_t test_stall;     /* testing only, split plans: the kernel waits once on a barrier nothing
                                arrives on, so its bounded wait expires and lrb_plan_status reports
                                LRB_ERR_TIMEOUT (exercises the failure path without a GPU fault) */
-    int32_t reserved[2];
+    int32_t trans;          /* FP64 plans: bit 0 set -> every entry multiplies A^T, with A stored
+                               k x m (lda >= k); bit 1 set -> B^T, with B stored n x k (ldb >= n).
+                               m, n, k are always the sizes of the product.  0 = both as stored.
+                               Plans with trans != 0 or overwrite != 0 have no plain launch. */
+    int32_t overwrite;      /* FP64 plans: 1 -> C = op(A) op(B) (old C is not read); 0 -> C += */
 } lrb_plan_opts;
 
 typedef struct lrb_handle lrb_handle;
@@ -272,6 +276,71 @@ lrb_status lrb_queue_stats(lrb_queue* q, lrb_queue_stats_t* out);
 /* Drains the queue (bounded by timeout_ms; < 0 means 600 s), stops the
  * worker and frees everything; LRB_ERR_TIMEOUT if it had to abandon work. */
 lrb_status lrb_queue_destroy(lrb_queue* q, int timeout_ms);
+
+/* ---- producers and consumers of low-rank blocks ---------------------------
+ * A block of shape (m, n, rank) is stored as U S V (Eq. 1, Sec. 3) with a
+ * diagonal S: U is m x r (ldu >= m), S holds r values, V is r x n (ldv >= r);
+ * device pointers, column-major.  Sec. 3 names the calls around the batched
+ * low-rank product: blocks are produced from dense ones by a randomized SVD
+ * (Halko, Martinsson and Tropp), and the low-rank product is the first step
+ * of the rounded addition of low-rank blocks.  Each call below plans a batch
+ * (host descriptor arrays, copied), runs on lrb_launch as a fixed sequence of
+ * batched kernels (the FP64 GEMM path for every product, a Householder QR
+ * kernel for the tall-skinny orthonormalisations, a one-sided Jacobi SVD
+ * kernel for the small l x l cores), and reports its flops through
+ * lrb_plan_get_info.  Outputs are WRITTEN and must not overlap any input or
+ * another output.  lrb_plan_status returns LRB_ERR_TIMEOUT when a Jacobi SVD
+ * used its whole sweep limit without converging (its last iterate is
+ * written).  Limits: l (and r1 + r2) <= LRB_LR_MAX_L, m, n <= LRB_LR_MAX_ROWS;
+ * larger requests return LRB_ERR_UNSUPPORTED before any CUDA call. */
+#define LRB_LR_MAX_L 96
+#define LRB_LR_MAX_ROWS 8192
+
+typedef struct lrb_lr_block {
+    double* U;
+    double* S;
+    double* V;
+    int32_t m, n, r;
+    int32_t ldu, ldv;
+    int32_t reserved;
+} lrb_lr_block;
+
+/* Randomized SVD of one dense block A (m x n, lda >= m): with the Gaussian
+ * test matrix Omega (n x l, ldo >= n; the caller draws it, r <= l <= min(m, n))
+ *   Y = A Omega, Q = orth(Y); q times: Q~ = orth(A^T Q), Q = orth(A Q~);
+ *   A^T Q = Q2 R2;  R2^T = U~ Sigma W^T (Jacobi);  U = Q U~[:, :r],
+ *   S = Sigma[:r] (descending),  V = (Q2 W[:, :r])^T
+ * which equals stage B's SVD of B = Q^T A = R2^T Q2^T.  out.m, out.n must
+ * equal m, n; out.r is the kept rank r. */
+typedef struct lrb_rsvd_desc {
+    const double* A;
+    const double* Omega;
+    lrb_lr_block out;
+    int32_t l, lda, ldo;
+    int32_t reserved;
+} lrb_rsvd_desc;
+lrb_status lrb_rsvd_plan_create(lrb_handle* h, const lrb_rsvd_desc* host_descs, size_t count,
+                                int32_t power_iters, lrb_plan** out);
+
+/* Expansion: D (m x n, ldd >= m) += U diag(S) V, computed as (U diag(S)) V. */
+typedef struct lrb_expand_desc {
+    lrb_lr_block blk;
+    double* D;
+    int32_t ldd;
+    int32_t reserved;
+} lrb_expand_desc;
+lrb_status lrb_expand_plan_create(lrb_handle* h, const lrb_expand_desc* host_descs, size_t count,
+                                  lrb_plan** out);
+
+/* Rounded addition: out = the rank-out.r truncation of x + y (same m, n):
+ *   [x.U diag(x.S), y.U diag(y.S)] = Q1 R1,  [x.V; y.V]^T = Q2 R2,
+ *   R1 R2^T = U~ Sigma W^T,  out.U = Q1 U~[:, :r], out.S = Sigma[:r],
+ *   out.V = (Q2 W[:, :r])^T;   r <= x.r + y.r <= min(m, n). */
+typedef struct lrb_round_add_desc {
+    lrb_lr_block x, y, out;
+} lrb_round_add_desc;
+lrb_status lrb_round_add_plan_create(lrb_handle* h, const lrb_round_add_desc* host_descs, size_t count,
+                                     lrb_plan** out);
 
 /* Message of the last failure on the calling thread ("" if none). */
 const char* lrb_last_error(void);

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "lrb_internal.h"
+#include "lowrank.h"
 #include "split.h"
 
 using namespace lrb;
@@ -80,6 +81,9 @@ lrb_status validate(const lrb_gemm_desc* d, size_t count, const lrb_plan_opts& o
     if (o.precision < LRB_PREC_FP64 || o.precision > LRB_PREC_SPLIT_FP16_S4)
         return fail(LRB_ERR_INVALID, "unknown precision");
     if (o.force_variant >= kNumVariants) return fail(LRB_ERR_INVALID, "force_variant out of range");
+    if (o.trans < 0 || o.trans > 3) return fail(LRB_ERR_INVALID, "trans must be 0..3");
+    if (o.overwrite < 0 || o.overwrite > 1) return fail(LRB_ERR_INVALID, "overwrite must be 0 or 1");
+    const bool ta = (o.trans & 1) != 0, tb = (o.trans & 2) != 0;
     std::vector<Range> cr, ab;
     if (o.check_alias) {
         cr.reserve(count);
@@ -100,13 +104,16 @@ lrb_status validate(const lrb_gemm_desc* d, size_t count, const lrb_plan_opts& o
             std::snprintf(buf, sizeof buf, "entry %zu: m, n, k must be >= 1 (got %d, %d, %d)", e, x.m, x.n, x.k);
             return fail(LRB_ERR_INVALID, buf);
         }
-        if (x.lda < x.m || x.ldb < x.k || x.ldc < x.m) {
+        // stored operands: A is m x k (k x m when transposed), B k x n (n x k)
+        const int32_t ar = ta ? x.k : x.m, ac = ta ? x.m : x.k;
+        const int32_t br = tb ? x.n : x.k, bc = tb ? x.k : x.n;
+        if (x.lda < ar || x.ldb < br || x.ldc < x.m) {
             std::snprintf(buf, sizeof buf, "entry %zu: leading dimension below rows (lda %d, ldb %d, ldc %d)", e,
                           x.lda, x.ldb, x.ldc);
             return fail(LRB_ERR_INVALID, buf);
         }
         Range ra, rb, rc;
-        if (!extent(x.A, x.m, x.k, x.lda, &ra) || !extent(x.B, x.k, x.n, x.ldb, &rb) ||
+        if (!extent(x.A, ar, ac, x.lda, &ra) || !extent(x.B, br, bc, x.ldb, &rb) ||
             !extent(x.C, x.m, x.n, x.ldc, &rc)) {
             std::snprintf(buf, sizeof buf, "entry %zu: operand extent overflows", e);
             return fail(LRB_ERR_INVALID, buf);
@@ -242,6 +249,7 @@ struct lrb_plan {
     int n_items = 0;
     int grid = 0;
     int set = 0;         // variant set of the persistent kernel (largest set of any tile)
+    int ops = 0;         // operand forms: bit 0 A^T, bit 1 B^T, bit 2 overwrite C (slim set only)
     std::vector<Group> groups;
     bool use_graph = false;
     cudaGraph_t graph = nullptr;
@@ -257,6 +265,8 @@ struct lrb_plan {
     void* lr_work = nullptr;           // unfused: C_temp and E_temp of every block
     size_t lr_work_bytes = 0;
     lrb_plan* lr_stage[3] = {nullptr, nullptr, nullptr};
+    // producer / consumer plans of low-rank blocks (randomized SVD, expansion, rounded addition)
+    lowrank::LrPlan* lp = nullptr;
 };
 
 namespace {
@@ -422,6 +432,9 @@ lrb_status choose_variants(lrb_handle* h, const lrb_gemm_desc* d, size_t count, 
         var[e] = v;
     }
     if (dirty) save_cache(h);
+    if (o.trans != 0 || o.overwrite != 0)   // those forms run in the slim persistent kernel only
+        for (int& v : var)
+            if (variant_set(v) != 0) v = kVariants[v].dmma ? 8 : 2;
     return LRB_OK;
 }
 
@@ -436,6 +449,7 @@ void free_plan(lrb_plan* p) {
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
     if (p->sp) split::destroy(p->sp);
+    if (p->lp) lowrank::destroy(p->lp);
     if (p->dmem) cudaFree(p->dmem);
     delete p;
 }
@@ -459,6 +473,12 @@ lrb::HandleInfo lrb::handle_info(const lrb_handle* h) {
     return HandleInfo{h->device, h->sms, h->blocks_per_sm, h->blocks_per_sm_wide, h->blocks_per_sm_slim};
 }
 lrb_plan_opts lrb::default_plan_opts() { return default_opts(); }
+cudaError_t lrb::enqueue_fp64_plan(lrb_plan* p, cudaStream_t s) {
+    if (p->sp || p->lp || p->lr_kind) return cudaErrorInvalidValue;
+    p->last_stream = s;
+    p->launched = true;
+    return launch_persistent(p->d_descs, p->d_items, p->n_items, p->d_head, p->grid, s, p->set, p->ops);
+}
 
 extern "C" {
 
@@ -590,6 +610,11 @@ lrb_status lrb_plan_create(lrb_handle* h, const lrb_gemm_desc* host_descs, size_
     p->info.alg_bytes = bytes;
     p->info.precision = o.precision;
 
+    if (o.precision >= LRB_PREC_SPLIT_BF16_S3 && (o.trans != 0 || o.overwrite != 0)) {
+        free_plan(p);
+        return fail(LRB_ERR_UNSUPPORTED, "split-precision plans take A and B as stored and accumulate into C");
+    }
+    p->ops = o.trans | (o.overwrite ? 4 : 0);
     if (o.precision >= LRB_PREC_SPLIT_BF16_S3) {
         s = split::create(h->device, h->sms, p->descs.data(), count, o.precision, &p->sp, &p->info, o.test_stall);
         if (s != LRB_OK) {
@@ -679,7 +704,8 @@ lrb_status lrb_plan_create(lrb_handle* h, const lrb_gemm_desc* host_descs, size_
         cudaStream_t cs = h->stream;
         ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (ce == cudaSuccess) {
-            cudaError_t le = launch_persistent(p->d_descs, p->d_items, p->n_items, p->d_head, p->grid, cs, p->set);
+            cudaError_t le =
+                launch_persistent(p->d_descs, p->d_items, p->n_items, p->d_head, p->grid, cs, p->set, p->ops);
             ce = cudaStreamEndCapture(cs, &p->graph);
             if (le != cudaSuccess) ce = le;
         }
@@ -704,6 +730,10 @@ lrb_status lrb_launch(lrb_plan* p, void* stream) {
         cudaError_t e = split::launch(p->sp, s);
         return e == cudaSuccess ? LRB_OK : cuda_fail(e, "split launch");
     }
+    if (p->lp) {
+        cudaError_t e = lowrank::launch(p->lp, s);
+        return e == cudaSuccess ? LRB_OK : cuda_fail(e, "low-rank plan launch");
+    }
     if (p->lr_kind == 1) {
         cudaError_t e = launch_lr_chain(p->d_lr, p->lr_count, s);
         return e == cudaSuccess ? LRB_OK : cuda_fail(e, "low-rank chain launch");
@@ -718,7 +748,8 @@ lrb_status lrb_launch(lrb_plan* p, void* stream) {
         return LRB_OK;
     }
     cudaError_t e = p->use_graph ? cudaGraphLaunch(p->exec, s)
-                                 : launch_persistent(p->d_descs, p->d_items, p->n_items, p->d_head, p->grid, s, p->set);
+                                 : launch_persistent(p->d_descs, p->d_items, p->n_items, p->d_head, p->grid, s,
+                                                     p->set, p->ops);
     if (e != cudaSuccess) return cuda_fail(e, "persistent launch");
     return LRB_OK;
 }
@@ -727,6 +758,8 @@ lrb_status lrb_launch_plain(lrb_plan* p, void* stream) {
     if (!p) return fail(LRB_ERR_INVALID, "plan is NULL");
     if (p->sp) return fail(LRB_ERR_UNSUPPORTED, "split-precision plans have no plain launch");
     if (p->lr_kind) return fail(LRB_ERR_UNSUPPORTED, "low-rank chain plans have no plain launch");
+    if (p->ops) return fail(LRB_ERR_UNSUPPORTED, "transposed or overwriting plans have no plain launch");
+    if (p->lp) return fail(LRB_ERR_UNSUPPORTED, "low-rank producer/consumer plans have no plain launch");
     cudaStream_t s = (cudaStream_t)stream;
     LRB_CUDA(cudaSetDevice(p->h->device));
     p->last_stream = s;
@@ -744,6 +777,8 @@ lrb_status lrb_execute_host(lrb_handle* h, const lrb_gemm_desc* host_descs, size
     if (!h) return fail(LRB_ERR_INVALID, "handle is NULL");
     const lrb_plan_opts o = opts ? *opts : default_opts();
     if (!host_descs || count == 0) return validate(host_descs, count, o);
+    if (o.trans != 0 || o.overwrite != 0)
+        return fail(LRB_ERR_UNSUPPORTED, "the host-buffer path takes A and B as stored and accumulates into C");
     lrb_status st = LRB_OK;
     LRB_CUDA(cudaSetDevice(h->device));
     cudaStream_t s = (cudaStream_t)stream;
@@ -941,7 +976,58 @@ lrb_status lrb_plan_status(lrb_plan* p) {
         if (split::read_status(p->sp, p->last_stream, &v) != 0) return fail(LRB_ERR_DEVICE, "reading plan status");
         if (v) return fail(LRB_ERR_TIMEOUT, "a bounded device wait expired in a split-precision launch");
     }
+    if (p->lp) {
+        int v = 0;
+        if (lowrank::read_status(p->lp, p->last_stream, &v) != 0) return fail(LRB_ERR_DEVICE, "reading plan status");
+        if (v) return fail(LRB_ERR_TIMEOUT, "a Jacobi SVD reached its sweep limit without converging");
+    }
     return LRB_OK;
+}
+
+namespace {
+lrb_status wrap_lowrank(lrb_handle* h, lowrank::LrPlan* lp, const lrb_plan_info& info, lrb_plan** out) {
+    lrb_plan* p = new (std::nothrow) lrb_plan();
+    if (!p) {
+        lowrank::destroy(lp);
+        return fail(LRB_ERR_NOMEM, "plan allocation");
+    }
+    p->h = h;
+    p->lp = lp;
+    p->info = info;
+    *out = p;
+    return LRB_OK;
+}
+}  // namespace
+
+lrb_status lrb_rsvd_plan_create(lrb_handle* h, const lrb_rsvd_desc* d, size_t count, int32_t power_iters,
+                                lrb_plan** out) {
+    if (!h || !out) return fail(LRB_ERR_INVALID, "NULL argument");
+    *out = nullptr;
+    LRB_CUDA(cudaSetDevice(h->device));
+    lowrank::LrPlan* lp = nullptr;
+    lrb_plan_info info{};
+    lrb_status s = lowrank::create_rsvd(h, d, count, power_iters, &lp, &info);
+    return s != LRB_OK ? s : wrap_lowrank(h, lp, info, out);
+}
+
+lrb_status lrb_expand_plan_create(lrb_handle* h, const lrb_expand_desc* d, size_t count, lrb_plan** out) {
+    if (!h || !out) return fail(LRB_ERR_INVALID, "NULL argument");
+    *out = nullptr;
+    LRB_CUDA(cudaSetDevice(h->device));
+    lowrank::LrPlan* lp = nullptr;
+    lrb_plan_info info{};
+    lrb_status s = lowrank::create_expand(h, d, count, &lp, &info);
+    return s != LRB_OK ? s : wrap_lowrank(h, lp, info, out);
+}
+
+lrb_status lrb_round_add_plan_create(lrb_handle* h, const lrb_round_add_desc* d, size_t count, lrb_plan** out) {
+    if (!h || !out) return fail(LRB_ERR_INVALID, "NULL argument");
+    *out = nullptr;
+    LRB_CUDA(cudaSetDevice(h->device));
+    lowrank::LrPlan* lp = nullptr;
+    lrb_plan_info info{};
+    lrb_status s = lowrank::create_round_add(h, d, count, &lp, &info);
+    return s != LRB_OK ? s : wrap_lowrank(h, lp, info, out);
 }
 
 lrb_status lrb_split_dump_levels(lrb_plan* p, float* dump, void* stream) {

@@ -63,24 +63,49 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Stage k-step kt of the tile (rows [m0, m0+BM) of A, cols [n0, n0+BN) of B)
-// into buffer `buf`; elements outside the entry are zero-filled.
-template <int BM, int BN>
+// Operand forms of a launch (template bits, uniform over the launch):
+// kTransA: A is stored k x m and the tile multiplies A^T; kTransB: B is
+// stored n x k (B^T); kOverwrite: C = op(A) op(B), the old C is not read.
+constexpr int kTransA = 1, kTransB = 2, kOverwrite = 4;
+
+// Stage k-step kt of the tile (rows [m0, m0+BM) of op(A), cols [n0, n0+BN)
+// of op(B)) into buffer `buf` as As[kk][ii], Bs[kk][jj]; elements outside the
+// entry are zero-filled.  Consecutive threads walk the stored matrix's
+// contiguous index, so every form reads whole 128-byte segments.
+template <int BM, int BN, int OPS>
 __device__ __forceinline__ void stage(const DevDesc& d, int m0, int n0, int h, int wc, int kt,
                                       double* As, double* Bs) {
     const int k0 = kt * kBK;
     const int kmax = min(kBK, d.k - k0);
-    for (int e = threadIdx.x; e < BM * kBK; e += kThreads) {
-        const int ii = e % BM, kk = e / BM;
-        const bool ok = ii < h && kk < kmax;
-        const double* src = ok ? d.A + (size_t)(m0 + ii) + (size_t)(k0 + kk) * (size_t)d.lda : d.A;
-        cp_async8(As + kk * BM + ii, src, ok);
+    if constexpr ((OPS & kTransA) != 0) {
+        for (int e = threadIdx.x; e < BM * kBK; e += kThreads) {
+            const int kk = e % kBK, ii = e / kBK;
+            const bool ok = ii < h && kk < kmax;
+            const double* src = ok ? d.A + (size_t)(k0 + kk) + (size_t)(m0 + ii) * (size_t)d.lda : d.A;
+            cp_async8(As + kk * BM + ii, src, ok);
+        }
+    } else {
+        for (int e = threadIdx.x; e < BM * kBK; e += kThreads) {
+            const int ii = e % BM, kk = e / BM;
+            const bool ok = ii < h && kk < kmax;
+            const double* src = ok ? d.A + (size_t)(m0 + ii) + (size_t)(k0 + kk) * (size_t)d.lda : d.A;
+            cp_async8(As + kk * BM + ii, src, ok);
+        }
     }
-    for (int e = threadIdx.x; e < kBK * BN; e += kThreads) {
-        const int kk = e % kBK, jj = e / kBK;
-        const bool ok = kk < kmax && jj < wc;
-        const double* src = ok ? d.B + (size_t)(k0 + kk) + (size_t)(n0 + jj) * (size_t)d.ldb : d.B;
-        cp_async8(Bs + kk * BN + jj, src, ok);
+    if constexpr ((OPS & kTransB) != 0) {
+        for (int e = threadIdx.x; e < kBK * BN; e += kThreads) {
+            const int jj = e % BN, kk = e / BN;
+            const bool ok = kk < kmax && jj < wc;
+            const double* src = ok ? d.B + (size_t)(n0 + jj) + (size_t)(k0 + kk) * (size_t)d.ldb : d.B;
+            cp_async8(Bs + kk * BN + jj, src, ok);
+        }
+    } else {
+        for (int e = threadIdx.x; e < kBK * BN; e += kThreads) {
+            const int kk = e % kBK, jj = e / kBK;
+            const bool ok = kk < kmax && jj < wc;
+            const double* src = ok ? d.B + (size_t)(k0 + kk) + (size_t)(n0 + jj) * (size_t)d.ldb : d.B;
+            cp_async8(Bs + kk * BN + jj, src, ok);
+        }
     }
     cp_async_commit();
 }
@@ -89,7 +114,7 @@ __device__ __forceinline__ void stage(const DevDesc& d, int m0, int n0, int h, i
 // wn*TN + j (j < TN) with wn = warp % WN; k-slice wk = warp / WN of every
 // k-step.  Accumulators start from C (slice 0) or 0 (other slices); slices
 // are added in slice order at the end.
-template <int TM, int TN, int WN, int SK>
+template <int TM, int TN, int WN, int SK, int OPS>
 __device__ __forceinline__ void tile_dfma(const DevDesc& d, int m0, int n0, double* smem) {
     constexpr int BM = 32 * TM, BN = WN * TN, KS = kBK / SK;
     static_assert(WN * SK == kThreads / 32, "4 warps");
@@ -108,7 +133,7 @@ __device__ __forceinline__ void tile_dfma(const DevDesc& d, int m0, int n0, doub
     for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
-    if (wk == 0) {
+    if (wk == 0 && (OPS & kOverwrite) == 0) {
 #pragma unroll
         for (int i = 0; i < TM; ++i) {
             const int row = lane + 32 * i;
@@ -122,11 +147,11 @@ __device__ __forceinline__ void tile_dfma(const DevDesc& d, int m0, int n0, doub
     }
 
     const int nk = (d.k + kBK - 1) / kBK;
-    stage<BM, BN>(d, m0, n0, h, wc, 0, As, Bs);
+    stage<BM, BN, OPS>(d, m0, n0, h, wc, 0, As, Bs);
     for (int kt = 0; kt < nk; ++kt) {
         const int buf = kt & 1;
         if (kt + 1 < nk) {
-            stage<BM, BN>(d, m0, n0, h, wc, kt + 1, As + (buf ^ 1) * kBK * BM, Bs + (buf ^ 1) * kBK * BN);
+            stage<BM, BN, OPS>(d, m0, n0, h, wc, kt + 1, As + (buf ^ 1) * kBK * BM, Bs + (buf ^ 1) * kBK * BN);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
@@ -213,7 +238,7 @@ __device__ __forceinline__ void tile_dfma(const DevDesc& d, int m0, int n0, doub
 // [16 w, 16 w + 16) of a 64 x (8 NF) tile as 2 x NF 8x8 fragments.
 // Fragment layout (PTX ISA, f64 m8n8k4): A(8x4): lane holds (lane>>2, lane&3);
 // B(4x8): (lane&3, lane>>2); C(8x8): (lane>>2, 2(lane&3) + {0,1}).
-template <int NF>
+template <int NF, int OPS>
 __device__ __forceinline__ void tile_dmma(const DevDesc& d, int m0, int n0, double* smem) {
     constexpr int BM = 64, BN = 8 * NF;
     double* As = smem;
@@ -234,18 +259,18 @@ __device__ __forceinline__ void tile_dmma(const DevDesc& d, int m0, int n0, doub
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 const int col = 8 * nf + 2 * q4 + q;
-                if (row < h && col < wc)
+                if ((OPS & kOverwrite) == 0 && row < h && col < wc)
                     acc[mi][nf][q] = d.C[(size_t)(m0 + row) + (size_t)(n0 + col) * (size_t)d.ldc];
             }
         }
     const bool mv0 = 16 * warp < h, mv1 = 16 * warp + 8 < h;
 
     const int nk = (d.k + kBK - 1) / kBK;
-    stage<BM, BN>(d, m0, n0, h, wc, 0, As, Bs);
+    stage<BM, BN, OPS>(d, m0, n0, h, wc, 0, As, Bs);
     for (int kt = 0; kt < nk; ++kt) {
         const int buf = kt & 1;
         if (kt + 1 < nk) {
-            stage<BM, BN>(d, m0, n0, h, wc, kt + 1, As + (buf ^ 1) * kBK * BM, Bs + (buf ^ 1) * kBK * BN);
+            stage<BM, BN, OPS>(d, m0, n0, h, wc, kt + 1, As + (buf ^ 1) * kBK * BM, Bs + (buf ^ 1) * kBK * BN);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
@@ -292,27 +317,28 @@ __device__ __forceinline__ void tile_dmma(const DevDesc& d, int m0, int n0, doub
 // fit 102 registers (5 CTAs = 20 warps per SM), SET 1 (narrow) adds the
 // 64x64 and 128x32 DFMA tiles (168 registers, 3 CTAs), SET 2 (wide) every
 // variant (1 CTA).
-template <int SET>
+template <int SET, int OPS>
 __device__ __forceinline__ void run_tile(int variant, const DevDesc& d, int m0, int n0, double* smem) {
     switch (variant) {
-        case 0: tile_dfma<2, 2, 4, 1>(d, m0, n0, smem); break;
-        case 1: tile_dfma<2, 4, 4, 1>(d, m0, n0, smem); break;
-        case 2: tile_dfma<2, 8, 4, 1>(d, m0, n0, smem); break;
-        case 3: if constexpr (SET >= 1) tile_dfma<2, 16, 4, 1>(d, m0, n0, smem); break;
-        case 4: if constexpr (SET >= 1) tile_dfma<4, 8, 4, 1>(d, m0, n0, smem); break;
-        case 5: if constexpr (SET >= 2) tile_dfma<4, 16, 4, 1>(d, m0, n0, smem); break;
-        case 6: tile_dfma<1, 8, 1, 4>(d, m0, n0, smem); break;
-        case 7: tile_dfma<1, 16, 2, 2>(d, m0, n0, smem); break;
-        case 8: tile_dmma<4>(d, m0, n0, smem); break;
-        case 9: if constexpr (SET >= 2) tile_dmma<8>(d, m0, n0, smem); break;
+        case 0: tile_dfma<2, 2, 4, 1, OPS>(d, m0, n0, smem); break;
+        case 1: tile_dfma<2, 4, 4, 1, OPS>(d, m0, n0, smem); break;
+        case 2: tile_dfma<2, 8, 4, 1, OPS>(d, m0, n0, smem); break;
+        case 3: if constexpr (SET >= 1) tile_dfma<2, 16, 4, 1, OPS>(d, m0, n0, smem); break;
+        case 4: if constexpr (SET >= 1) tile_dfma<4, 8, 4, 1, OPS>(d, m0, n0, smem); break;
+        case 5: if constexpr (SET >= 2) tile_dfma<4, 16, 4, 1, OPS>(d, m0, n0, smem); break;
+        case 6: tile_dfma<1, 8, 1, 4, OPS>(d, m0, n0, smem); break;
+        case 7: tile_dfma<1, 16, 2, 2, OPS>(d, m0, n0, smem); break;
+        case 8: tile_dmma<4, OPS>(d, m0, n0, smem); break;
+        case 9: if constexpr (SET >= 2) tile_dmma<8, OPS>(d, m0, n0, smem); break;
         default: break;   // planner never emits other ids
     }
 }
 
 // Persistent kernel: each CTA takes the next tile from the work counter until
 // the list (ordered longest-first by the planner) is exhausted.  No CTA ever
-// waits for another; the counter is the only shared state.
-template <int SET>
+// waits for another; the counter is the only shared state.  OPS (operand
+// forms, above) is instantiated beyond 0 for the slim set only.
+template <int SET, int OPS>
 __global__ void __launch_bounds__(kThreads, SET == 0 ? 5 : SET == 1 ? 3 : 1) k_persistent(const DevDesc* __restrict__ descs,
                                                                       const Item* __restrict__ items, int n_items,
                                                                       int* __restrict__ head) {
@@ -326,7 +352,7 @@ __global__ void __launch_bounds__(kThreads, SET == 0 ? 5 : SET == 1 ? 3 : 1) k_p
         const DevDesc d = descs[item.entry];
         __syncthreads();                                   // every thread has read s_item
         if (threadIdx.x == 0) s_item = atomicAdd(head, 1);  // claim the next tile while this one runs
-        run_tile<SET>(item.variant, d, item.row0, item.col0, smem);
+        run_tile<SET, OPS>(item.variant, d, item.row0, item.col0, smem);
         __syncthreads();
         it = s_item;
     }
@@ -345,7 +371,7 @@ __global__ void __launch_bounds__(kThreads) k_plain(const DevDesc* __restrict__ 
     const int bm = (V == 8 || V == 9) ? 64 : (V == 4 || V == 5 ? 128 : (V >= 6 ? 32 : 64));
     const int bn = V == 0 ? 8 : V == 1 ? 16 : V == 2 ? 32 : V == 3 ? 64 : V == 4 ? 32 : V == 5 ? 64
                  : V == 6 ? 8 : V == 7 ? 32 : V == 8 ? 32 : 64;
-    run_tile<2>(V, d, (t % tiles_m) * bm, (t / tiles_m) * bn, smem);
+    run_tile<2, 0>(V, d, (t % tiles_m) * bm, (t / tiles_m) * bn, smem);
 }
 
 template <int V>
@@ -373,35 +399,58 @@ size_t persistent_smem_bytes(int set) {
 }
 
 namespace {
-template <int SET>
+template <int SET, int OPS>
 int blocks_for() {
     int nb = 0;
     const size_t smem = persistent_smem_bytes(SET);
-    if (cudaFuncSetAttribute(k_persistent<SET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_persistent<SET, OPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<SET>, kThreads, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<SET, OPS>, kThreads, smem) != cudaSuccess)
+        return 0;
     return nb;
 }
 }  // namespace
 
 int persistent_blocks_per_sm(int set) {
-    return set <= 0 ? blocks_for<0>() : set == 1 ? blocks_for<1>() : blocks_for<2>();
+    if (set >= 2) return blocks_for<2, 0>();
+    if (set == 1) return blocks_for<1, 0>();
+    // the slim set also serves the transposed / overwriting forms: every
+    // instantiation gets its shared-memory attribute here; the launch
+    // uses the smallest residency of them
+    int nb = blocks_for<0, 0>();
+    nb = std::min(nb, blocks_for<0, 1>());
+    nb = std::min(nb, blocks_for<0, 2>());
+    nb = std::min(nb, blocks_for<0, 3>());
+    nb = std::min(nb, blocks_for<0, 4>());
+    nb = std::min(nb, blocks_for<0, 5>());
+    nb = std::min(nb, blocks_for<0, 6>());
+    nb = std::min(nb, blocks_for<0, 7>());
+    return nb;
 }
 
 cudaError_t launch_persistent(const DevDesc* d_descs, const Item* d_items, int n_items, int* d_head, int grid,
-                              cudaStream_t s, int set) {
+                              cudaStream_t s, int set, int ops) {
     // the shared-memory attribute was set by persistent_blocks_per_sm() when
     // the handle was created (not here: this may run under stream capture)
+    if (ops < 0 || ops > 7 || (ops != 0 && set != 0)) return cudaErrorInvalidValue;
     const size_t smem = persistent_smem_bytes(set);
     cudaError_t e = cudaMemsetAsync(d_head, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     if (n_items <= 0) return cudaSuccess;
-    if (set <= 0)
-        k_persistent<0><<<grid, kThreads, smem, s>>>(d_descs, d_items, n_items, d_head);
-    else if (set == 1)
-        k_persistent<1><<<grid, kThreads, smem, s>>>(d_descs, d_items, n_items, d_head);
-    else
-        k_persistent<2><<<grid, kThreads, smem, s>>>(d_descs, d_items, n_items, d_head);
+    const dim3 g(grid), b(kThreads);
+    switch (set <= 0 ? ops : 8 + set) {
+        case 0: k_persistent<0, 0><<<g, b, smem, s>>>(d_descs, d_items, n_items, d_head); break;
+        case 1: k_persistent<0, 1><<<g, b, smem, s>>>(d_descs, d_items, n_items, d_head); break;
+        case 2: k_persistent<0, 2><<<g, b, smem, s>>>(d_descs, d_items, n_items, d_head); break;
+        case 3: k_persistent<0, 3><<<g, b, smem, s>>>(d_descs, d_items, n_items, d_head); break;
+        case 4: k_persistent<0, 4><<<g, b, smem, s>>>(d_descs, d_items, n_items, d_head); break;
+        case 5: k_persistent<0, 5><<<g, b, smem, s>>>(d_descs, d_items, n_items, d_head); break;
+        case 6: k_persistent<0, 6><<<g, b, smem, s>>>(d_descs, d_items, n_items, d_head); break;
+        case 7: k_persistent<0, 7><<<g, b, smem, s>>>(d_descs, d_items, n_items, d_head); break;
+        case 9: k_persistent<1, 0><<<g, b, smem, s>>>(d_descs, d_items, n_items, d_head); break;
+        default: k_persistent<2, 0><<<g, b, smem, s>>>(d_descs, d_items, n_items, d_head); break;
+    }
     return cudaGetLastError();
 }
 

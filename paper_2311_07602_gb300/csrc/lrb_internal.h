@@ -7,7 +7,9 @@
 
 namespace lrb {
 
-// Device copy of one entry; the same field layout as lrb_gemm_desc.
+// Device copy of one entry; the same field layout as lrb_gemm_desc.  m, n, k
+// are the product's sizes; with transposed forms lda / ldb describe the
+// stored (transposed) operand.
 struct DevDesc {
     const double* A;
     const double* B;
@@ -63,8 +65,9 @@ size_t max_smem_bytes();
 // Kernel launchers (fp64_tiles.cu).
 // set: the variant set of the persistent kernel (variant_set); 0 slim (5
 // CTAs per SM), 1 narrow (3 CTAs, the default), 2 wide (every variant).
+// ops: operand forms (bit 0 A^T, bit 1 B^T, bit 2 overwrite C), slim set only.
 cudaError_t launch_persistent(const DevDesc* d_descs, const Item* d_items, int n_items,
-                              int* d_head, int grid, cudaStream_t s, int set = 1);
+                              int* d_head, int grid, cudaStream_t s, int set = 1, int ops = 0);
 cudaError_t launch_plain_group(int variant, const DevDesc* d_descs, const int32_t* d_entries,
                                int n_entries, int tiles_m, int tiles_n, cudaStream_t s);
 int persistent_blocks_per_sm(int set = 1);
@@ -89,6 +92,9 @@ lrb_status validate_descs(const lrb_gemm_desc* d, size_t count, const lrb_plan_o
 // Tile variant per entry (tuned-cache lookup, else tuning or the heuristic as o.tune says).
 lrb_status plan_variants(lrb_handle* h, const lrb_gemm_desc* d, size_t count, const lrb_plan_opts& o,
                          std::vector<int>& var);
+// Enqueues an FP64 plan's persistent launch on `s` (no device switch: safe
+// inside a stream capture); cudaErrorInvalidValue for other plan kinds.
+cudaError_t enqueue_fp64_plan(lrb_plan* p, cudaStream_t s);
 // Output tiles of all entries, longest first.
 void plan_tiles(const lrb_gemm_desc* d, size_t count, const std::vector<int>& var, std::vector<Item>& items);
 

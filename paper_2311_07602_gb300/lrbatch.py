@@ -40,11 +40,26 @@ DESC_DTYPE = np.dtype([("A", np.uint64), ("B", np.uint64), ("C", np.uint64), ("m
                        ("k", np.int32), ("lda", np.int32), ("ldb", np.int32), ("ldc", np.int32)])
 assert DESC_DTYPE.itemsize == 48
 
+# lrb_lr_block: U, S, V pointers then m, n, r, ldu, ldv, reserved (48 bytes)
+LR_BLOCK_DTYPE = np.dtype([("U", np.uint64), ("S", np.uint64), ("V", np.uint64), ("m", np.int32), ("n", np.int32),
+                           ("r", np.int32), ("ldu", np.int32), ("ldv", np.int32), ("reserved", np.int32)])
+assert LR_BLOCK_DTYPE.itemsize == 48
+# lrb_rsvd_desc (80 bytes), lrb_expand_desc (64), lrb_round_add_desc (144)
+RSVD_DESC_DTYPE = np.dtype([("A", np.uint64), ("Omega", np.uint64), ("out", LR_BLOCK_DTYPE), ("l", np.int32),
+                            ("lda", np.int32), ("ldo", np.int32), ("reserved", np.int32)])
+assert RSVD_DESC_DTYPE.itemsize == 80
+EXPAND_DESC_DTYPE = np.dtype([("blk", LR_BLOCK_DTYPE), ("D", np.uint64), ("ldd", np.int32), ("reserved", np.int32)])
+assert EXPAND_DESC_DTYPE.itemsize == 64
+ROUND_ADD_DESC_DTYPE = np.dtype([("x", LR_BLOCK_DTYPE), ("y", LR_BLOCK_DTYPE), ("out", LR_BLOCK_DTYPE)])
+assert ROUND_ADD_DESC_DTYPE.itemsize == 144
+LR_MAX_L = 96          # LRB_LR_MAX_L
+LR_MAX_ROWS = 8192     # LRB_LR_MAX_ROWS
+
 
 class lrb_plan_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("tune", ctypes.c_int32),
                 ("force_variant", ctypes.c_int32), ("check_alias", ctypes.c_int32),
-                ("test_stall", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("test_stall", ctypes.c_int32), ("trans", ctypes.c_int32), ("overwrite", ctypes.c_int32)]
 
 
 class lrb_plan_info(ctypes.Structure):
@@ -91,6 +106,9 @@ def lib():
             "lrb_launch_noalloc": ([vp, sz, vp], i32),
             "lrb_plan_status": ([vp], i32),
             "lrb_lr_plan_create": ([vp, vp, sz, i32, ctypes.POINTER(vp)], i32),
+            "lrb_rsvd_plan_create": ([vp, vp, sz, i32, ctypes.POINTER(vp)], i32),
+            "lrb_expand_plan_create": ([vp, vp, sz, ctypes.POINTER(vp)], i32),
+            "lrb_round_add_plan_create": ([vp, vp, sz, ctypes.POINTER(vp)], i32),
             "lrb_queue_create": ([vp, sz, ctypes.c_int, ctypes.POINTER(vp)], i32),
             "lrb_queue_set_limits": ([vp, sz, sz], i32),
             "lrb_queue_set_precision": ([vp, i32], i32),
@@ -131,9 +149,11 @@ def check(status):
 
 
 def make_opts(precision=LRB_PREC_FP64, use_graph=False, tune=True, force_variant=-1, check_alias=True,
-              test_stall=False):
+              test_stall=False, trans=0, overwrite=False):
     o = lrb_plan_opts()
     o.test_stall = int(bool(test_stall))
+    o.trans = int(trans)
+    o.overwrite = int(bool(overwrite))
     o.precision = precision
     o.use_graph = int(bool(use_graph))
     o.tune = int(bool(tune))
@@ -287,6 +307,28 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class LowRankPlan(Plan):
+    """lrb_rsvd_plan_create / lrb_expand_plan_create / lrb_round_add_plan_create:
+    kind "rsvd" (descs: RSVD_DESC_DTYPE rows, power_iters), "expand"
+    (EXPAND_DESC_DTYPE) or "round_add" (ROUND_ADD_DESC_DTYPE).  Launch,
+    status, info and close as for Plan."""
+
+    _KINDS = {"rsvd": RSVD_DESC_DTYPE, "expand": EXPAND_DESC_DTYPE, "round_add": ROUND_ADD_DESC_DTYPE}
+
+    def __init__(self, handle: Handle, kind: str, descs: np.ndarray, power_iters: int = 0):
+        self.handle = handle
+        self.ptr = ctypes.c_void_p()
+        self.descs = np.ascontiguousarray(descs, dtype=self._KINDS[kind])
+        d = self.descs.ctypes.data if len(self.descs) else None
+        if kind == "rsvd":
+            st = lib().lrb_rsvd_plan_create(handle.ptr, d, len(self.descs), int(power_iters), ctypes.byref(self.ptr))
+        elif kind == "expand":
+            st = lib().lrb_expand_plan_create(handle.ptr, d, len(self.descs), ctypes.byref(self.ptr))
+        else:
+            st = lib().lrb_round_add_plan_create(handle.ptr, d, len(self.descs), ctypes.byref(self.ptr))
+        check(st)
 
 
 class Queue:

@@ -255,3 +255,33 @@ def lr_batch(batch: int, b: int, r: int, *, rb: int = None, seed: int = 0, devic
         offs[key] = np.arange(batch, dtype=np.int64) * size
     full = lambda v: np.full(batch, v, dtype=np.int32)
     return LrBatch(bufs, offs, full(r), full(rb), full(b), pad)
+
+
+# ---- dense blocks for the low-rank producers --------------------------------
+# Sec. 3: low-rank blocks come from dense blocks whose singular values decay
+# fast, as the off-diagonal (admissible) blocks of hierarchical matrices do.
+# Stand-in: the Laplace kernel 1/|x - y| between two separated point clusters
+# (x uniform in the unit cube, y in the unit cube shifted by `sep` along the
+# first axis), evaluated element by element; no product is formed.
+
+def kernel_blocks(count: int, m: int, n: int, *, seed: int = 7, sep: float = 2.0, device="cpu",
+                  chunk: int = 64) -> torch.Tensor:
+    """`count` dense m x n blocks A_e[i, j] = 1 / |x_i - y_j|, column-major and
+    back to back (entry e at offset e m n, ld = m), float64."""
+    g = _gen(seed, device)
+    out = torch.empty(count * m * n, dtype=torch.float64, device=device)
+    shift = torch.tensor([sep, 0.0, 0.0], dtype=torch.float64, device=device)
+    for c0 in range(0, count, chunk):
+        c = min(chunk, count - c0)
+        x = torch.rand((c, m, 3), generator=g, dtype=torch.float64, device=device)
+        y = torch.rand((c, n, 3), generator=g, dtype=torch.float64, device=device) + shift
+        d = torch.cdist(y, x, compute_mode="donot_use_mm_for_euclid_dist")    # [c, n, m]: (j, i) -> j m + i
+        out[c0 * m * n:(c0 + c) * m * n] = d.reciprocal_().reshape(-1)
+    return out
+
+
+def gaussian_test_matrix(n: int, l: int, *, seed: int = 8, device="cpu") -> torch.Tensor:
+    """The randomized SVD's n x l test matrix Omega: N(0, 1), column-major
+    (ld = n), drawn from its own seeded generator."""
+    g = _gen(seed, device)
+    return torch.randn(n * l, generator=g, dtype=torch.float64, device=device)

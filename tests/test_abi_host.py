@@ -98,3 +98,30 @@ def test_tiles_cover_every_output_once(variant):
     else:
         cost = np.ceil(hh / 32) * 32 * tiles[:, 4] * k
     assert np.all(np.diff(cost) <= 0)
+
+
+def test_transposed_forms_validate_stored_shapes():
+    # m = 4, n = 3, k = 2.  A^T: A stored k x m (lda >= k = 2); B^T: B stored n x k (ldb >= n = 3)
+    base = (0x100000, 0x200000, 0x300000, 4, 3, 2)
+    ok = {0: (4, 2, 4), 1: (2, 2, 4), 2: (4, 3, 4), 3: (2, 3, 4)}
+    for trans, lds in ok.items():
+        o = L.make_opts(trans=trans)
+        assert L.lrb_validate(descs(base + lds), o) == L.LRB_OK, trans
+    # lda = 2 < m is fine only when A is transposed; ldb = 2 < n fails when B is
+    assert L.lrb_validate(descs(base + (2, 2, 4)), L.make_opts(trans=0)) == L.LRB_ERR_INVALID
+    assert L.lrb_validate(descs(base + (4, 2, 4)), L.make_opts(trans=2)) == L.LRB_ERR_INVALID
+    assert L.lrb_validate(descs(base + (1, 3, 4)), L.make_opts(trans=3)) == L.LRB_ERR_INVALID
+    assert L.lrb_validate(descs(base + (4, 2, 4)), L.make_opts(trans=4)) == L.LRB_ERR_INVALID
+    o = L.make_opts()
+    o.overwrite = 2
+    assert L.lrb_validate(descs(base + (4, 2, 4)), o) == L.LRB_ERR_INVALID
+
+
+def test_transposed_alias_uses_stored_extent():
+    # m = 2, n = 1, k = 3, lda = 10.  A as stored m x k spans 10*(3-1)+2 = 22
+    # elements; A^T stored k x m spans 10*(2-1)+3 = 13.  A C at element 15
+    # overlaps only the first.
+    A = 0x100000
+    d = descs((A, 0x200000, A + 8 * 15, 2, 1, 3, 10, 3, 2))
+    assert L.lrb_validate(d, L.make_opts(trans=0)) == L.LRB_ERR_ALIAS
+    assert L.lrb_validate(d, L.make_opts(trans=1)) == L.LRB_OK
