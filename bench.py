@@ -182,12 +182,14 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other workloads (64-entry O-form, variable-size, split precision, serving)")
-    ap.add_argument("--extras", default="small,variable,split,serving,dmma,lr,blr",
+    ap.add_argument("--extras", default="small,variable,split,serving,dmma,lr,blr,lowrank",
                     help="comma-separated subset of the other workloads to run")
     ap.add_argument("--split-batch", type=int, default=2048, help="entries of the split-precision batch")
     ap.add_argument("--dmma-scale", type=float, default=0.25, help="batch-count scale of the DMMA comparison")
     ap.add_argument("--lr-batch", type=int, default=20000, help="blocks per low-rank chain configuration")
     ap.add_argument("--lr-ranks", default="8,16,32,96,128", help="ranks of the low-rank chain sweep")
+    ap.add_argument("--lowrank-count", type=int, default=1024,
+                    help="dense blocks of the randomized-SVD / expansion / rounded-addition leg")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="batch-count scale of every group (profiling runs use a small case)")
     args = ap.parse_args()
@@ -304,7 +306,8 @@ def main():
         del batches
         torch.cuda.empty_cache()
         line["extras"] = extras(L, handle, stream, dev, peak, timed, set(args.extras.split(",")), args.split_batch,
-                                args.dmma_scale, args.lr_batch, tuple(int(x) for x in args.lr_ranks.split(",")))
+                                args.dmma_scale, args.lr_batch, tuple(int(x) for x in args.lr_ranks.split(",")),
+                                args.lowrank_count)
 
     if not args.no_cpu and rank == 0 and world == 1:
         f, s, used, ents = cpu_baseline(args.cpu_fraction)
@@ -322,7 +325,7 @@ def main():
 
 
 def extras(L, handle, stream, dev, peak_fp64, timed, which, split_batch, dmma_scale=0.25, lr_batch=20000,
-           lr_ranks=(8, 16, 32, 96, 128)):
+           lr_ranks=(8, 16, 32, 96, 128), lowrank_count=1024):
     """The other workloads, each with its own plan, 3 warm-up and 5 timed launches:
     the 64-entry O-form batch (L2 flushed before every launch: it fits in L2),
     the 20,000-entry variable-size batch (persistent vs one launch per shape),
@@ -351,6 +354,90 @@ def extras(L, handle, stream, dev, peak_fp64, timed, which, split_batch, dmma_sc
         out["lr_chain"] = lr_leg(L, handle, dev, peak_fp64, timed, lr_batch, lr_ranks)
     if "blr" in which:
         out["blr_matvec"] = blr_leg(L, handle, dev, peak_fp64, timed)
+    if "lowrank" in which:
+        out["lowrank"] = lowrank_leg(L, handle, dev, peak_fp64, timed, count=lowrank_count)
+    return out
+
+
+def lowrank_leg(L, handle, dev, peak_fp64, timed, count=1024, b=1024, r=16, p=10, q=1):
+    """Producers and consumers of low-rank blocks (Sec. 3): the randomized SVD
+    of `count` dense b x b blocks of the Laplace kernel 1/|x - y| between two
+    separated point clusters (the admissible blocks of a hierarchical matrix)
+    to rank r with p oversampling columns and q power iterations; the
+    expansion D += U diag(S) V, run with -S on D = A so that it leaves the
+    approximation residual A - U S V; and the rounded addition of the produced
+    blocks in pairs back to rank r.  GFLOP/s count what lrb_plan_get_info
+    reports (products with A, QRs, final products; 2 m n r per expansion)."""
+    import torch
+    from paper_2311_07602_gb300 import workloads as W
+    l = r + p
+    A = W.kernel_blocks(count, b, b, seed=7, device=dev)
+    Om = W.gaussian_test_matrix(b, l, seed=8, device=dev)
+    U = torch.empty(count * b * r, dtype=torch.float64, device=dev)
+    S = torch.empty(count * r, dtype=torch.float64, device=dev)
+    V = torch.empty(count * r * b, dtype=torch.float64, device=dev)
+    e = np.arange(count, dtype=np.uint64)
+    blk = np.zeros(count, dtype=L.LR_BLOCK_DTYPE)
+    blk["U"] = np.uint64(U.data_ptr()) + np.uint64(8 * b * r) * e
+    blk["S"] = np.uint64(S.data_ptr()) + np.uint64(8 * r) * e
+    blk["V"] = np.uint64(V.data_ptr()) + np.uint64(8 * r * b) * e
+    blk["m"], blk["n"], blk["r"], blk["ldu"], blk["ldv"] = b, b, r, b, r
+    d = np.zeros(count, dtype=L.RSVD_DESC_DTYPE)
+    d["A"] = np.uint64(A.data_ptr()) + np.uint64(8 * b * b) * e
+    d["Omega"] = Om.data_ptr()
+    d["out"] = blk
+    d["l"], d["lda"], d["ldo"] = l, b, b
+    out = {"workload": f"{count} Laplace-kernel blocks 1/|x - y| ({b} x {b}, clusters 2 apart), rank {r}, "
+                       f"oversampling {p}, {q} power iteration(s), Omega N(0,1)"}
+    with L.LowRankPlan(handle, "rsvd", d, power_iters=q) as pl:
+        info = pl.info()
+        ms, _ = timed(lambda s: pl.launch(s), 3, 2)
+        ms /= 3
+        assert pl.status() == L.LRB_OK
+    out["rsvd"] = {"ms": round(ms, 3), "gflops": round(info["flops"] / ms / 1e6, 1),
+                   "frac_fp64_peak": round(info["flops"] / ms / 1e9 / peak_fp64, 4),
+                   "blocks_per_s": round(count / ms * 1e3, 1), "flops_per_block": info["flops"] / count}
+    # expansion: D = A, S -> -S, so one launch leaves D = A - U S V
+    D = A.clone()
+    Sneg = -S
+    ed = np.zeros(count, dtype=L.EXPAND_DESC_DTYPE)
+    ed["blk"] = blk
+    ed["blk"]["S"] = np.uint64(Sneg.data_ptr()) + np.uint64(8 * r) * e
+    ed["D"] = np.uint64(D.data_ptr()) + np.uint64(8 * b * b) * e
+    ed["ldd"] = b
+    with L.LowRankPlan(handle, "expand", ed) as pl:
+        info = pl.info()
+        pl.launch()
+        torch.cuda.synchronize()
+        res = (D.view(count, b * b).norm(dim=1) / A.view(count, b * b).norm(dim=1)).cpu().numpy()
+        ms, _ = timed(lambda s: pl.launch(s), 3, 2)
+        ms /= 3
+    out["expand"] = {"ms": round(ms, 3), "gflops": round(info["flops"] / ms / 1e6, 1),
+                     "frac_fp64_peak": round(info["flops"] / ms / 1e9 / peak_fp64, 4)}
+    out["rel_residual_fro"] = {"median": float(np.median(res)), "max": float(res.max())}
+    del D, Sneg
+    # rounded addition of blocks (2i, 2i + 1) back to rank r
+    half = count // 2
+    U2 = torch.empty(half * b * r, dtype=torch.float64, device=dev)
+    S2 = torch.empty(half * r, dtype=torch.float64, device=dev)
+    V2 = torch.empty(half * r * b, dtype=torch.float64, device=dev)
+    h = np.arange(half, dtype=np.uint64)
+    ra = np.zeros(half, dtype=L.ROUND_ADD_DESC_DTYPE)
+    ra["x"], ra["y"] = blk[0::2], blk[1::2]
+    ra["out"]["U"] = np.uint64(U2.data_ptr()) + np.uint64(8 * b * r) * h
+    ra["out"]["S"] = np.uint64(S2.data_ptr()) + np.uint64(8 * r) * h
+    ra["out"]["V"] = np.uint64(V2.data_ptr()) + np.uint64(8 * r * b) * h
+    ra["out"]["m"], ra["out"]["n"], ra["out"]["r"], ra["out"]["ldu"], ra["out"]["ldv"] = b, b, r, b, r
+    with L.LowRankPlan(handle, "round_add", ra) as pl:
+        info = pl.info()
+        ms, _ = timed(lambda s: pl.launch(s), 3, 2)
+        ms /= 3
+        assert pl.status() == L.LRB_OK
+    out["round_add"] = {"pairs": half, "ms": round(ms, 3), "gflops": round(info["flops"] / ms / 1e6, 1),
+                        "frac_fp64_peak": round(info["flops"] / ms / 1e9 / peak_fp64, 4),
+                        "pairs_per_s": round(half / ms * 1e3, 1)}
+    del A, U, S, V, U2, S2, V2
+    torch.cuda.empty_cache()
     return out
 
 

@@ -17,6 +17,7 @@
 // The same tile functions serve the persistent work-queue kernel and the
 // one-launch-per-shape kernels, so both give bitwise identical results.
 #include <algorithm>
+#include <type_traits>
 
 #include "lrb_internal.h"
 
@@ -174,6 +175,43 @@ __device__ __forceinline__ void tile_dfma(const DevDesc& d, int m0, int n0, doub
                 for (int i = 0; i < TM; ++i)
 #pragma unroll
                     for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            }
+        } else if constexpr (TM * TN <= 16) {
+            // Partial tile.  A guard inside one k loop compiles to predicated
+            // DFMAs, which occupy the FP64 pipe like executed ones; so each
+            // pair of columns gets its own k loop behind a warp-uniform branch
+            // (at most one column per warp is wasted), and a tile with fewer
+            // valid row slots than TM (here TM <= 2: one slot) runs a loop over
+            // that slot alone.  Each accumulator still sums over kk in the
+            // same order.  (Tiles with more accumulators keep the single loop
+            // below: this form would push them into local memory.)
+            auto column_pairs = [&](auto rows_c) {
+                constexpr int R = decltype(rows_c)::value;
+#pragma unroll
+                for (int g = 0; g < TN; g += 2) {
+                    if (g < nj) {
+                        for (int kk = kb; kk < ke; ++kk) {
+                            double a[R];
+#pragma unroll
+                            for (int i = 0; i < R; ++i) a[i] = as[kk * BM + 32 * i];
+                            const double b0 = bs[kk * BN + g];
+                            const double b1 = TN > 1 ? bs[kk * BN + g + 1] : 0.0;
+#pragma unroll
+                            for (int i = 0; i < R; ++i) {
+                                acc[i][g] = fma(a[i], b0, acc[i][g]);
+                                if (TN > 1) acc[i][g + 1] = fma(a[i], b1, acc[i][g + 1]);
+                            }
+                        }
+                    }
+                }
+            };
+            if constexpr (TM == 1) {
+                column_pairs(std::integral_constant<int, 1>());
+            } else {
+                if (ni == TM)
+                    column_pairs(std::integral_constant<int, TM>());
+                else
+                    column_pairs(std::integral_constant<int, 1>());
             }
         } else {
             for (int kk = kb; kk < ke; ++kk) {

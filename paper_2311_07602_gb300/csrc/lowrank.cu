@@ -57,11 +57,11 @@ struct PackDesc {          // dst = [src1 diag(s1), src2 diag(s2)] or its transp
     int32_t rows, c1, c2, ld1, ld2, ldd;
 };
 
-constexpr int kQrThreads = 256;
+constexpr int kQrThreads = 512;
 constexpr int kQrWarps = kQrThreads / 32;
-constexpr int kSvdThreads = 256;
-constexpr int kSvdWarps = kSvdThreads / 32;
+constexpr int kSvdThreads = 512;
 constexpr int kMaxSweeps = 40;
+constexpr int kMaxPairs = (LRB_LR_MAX_L + 1) / 2;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -93,40 +93,81 @@ __device__ double block_max(double v, double* red) {
     return t;
 }
 
+// One warp applies H = I - tau v v^T to rows [j, m) of column y:
+// y <- y - tau (v^T y) v, with four independent partial sums so that the
+// loads of a column are in flight together.
+__device__ __forceinline__ void reflect_column(const double* __restrict__ v, double* y, int j, int m, double tau,
+                                               int lane) {
+    double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+    int i = j + lane;
+    for (; i + 96 < m; i += 128) {
+        d0 = fma(v[i], y[i], d0);
+        d1 = fma(v[i + 32], y[i + 32], d1);
+        d2 = fma(v[i + 64], y[i + 64], d2);
+        d3 = fma(v[i + 96], y[i + 96], d3);
+    }
+    for (; i < m; i += 32) d0 = fma(v[i], y[i], d0);
+    const double t = tau * warp_sum((d0 + d1) + (d2 + d3));
+    for (i = j + lane; i + 96 < m; i += 128) {
+        y[i] = fma(-t, v[i], y[i]);
+        y[i + 32] = fma(-t, v[i + 32], y[i + 32]);
+        y[i + 64] = fma(-t, v[i + 64], y[i + 64]);
+        y[i + 96] = fma(-t, v[i + 96], y[i + 96]);
+    }
+    for (; i < m; i += 32) y[i] = fma(-t, v[i], y[i]);
+}
+
 // Householder QR of one tall matrix per CTA (rows >= cols), the reflectors
 // H_j = I - tau_j v_j v_j^T with v_j(j) = 1 chosen so H_j x = beta e_j,
 // beta = -sign(x_j) ||x|| (Golub and Van Loan, Sec. 5.1), applied column by
-// column (a warp per trailing column: one dot product, one update).  Then
-// R is copied out and Q = H_0 ... H_{cols-1} [I; 0] is formed in place,
-// backwards.  A zero column gives tau = 0 (H = I), so rank-deficient input
-// still yields an orthonormal Q.  Dynamic shared memory: v (rows doubles).
+// column (a warp per trailing column).  Then R is copied out and
+// Q = H_0 ... H_{cols-1} [I; 0] is formed in place, backwards.  A zero column
+// gives tau = 0 (H = I), so rank-deficient input still yields an orthonormal
+// Q.  SMEM: the whole panel is staged in shared memory (rows x (cols + 1)
+// doubles with v), else it is worked on in place in global memory (L2).
+template <bool SMEM>
 __global__ void __launch_bounds__(kQrThreads) k_house_qr(const QrDesc* __restrict__ descs) {
-    extern __shared__ __align__(16) double v[];
+    extern __shared__ __align__(16) double sm[];
     __shared__ double red[kQrWarps];
     __shared__ double s_tau[LRB_LR_MAX_L];
     const QrDesc d = descs[blockIdx.x];
     const int m = d.rows, l = d.cols;
-    const size_t ld = (size_t)d.ldy;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    double* Y = d.Y;
+    double* v = sm;
+    double* P = d.Y;
+    size_t ld = (size_t)d.ldy;
+    if constexpr (SMEM) {
+        P = sm + m;
+        for (int e = tid; e < m * l; e += kQrThreads) P[e] = d.Y[(size_t)(e % m) + (size_t)(e / m) * ld];
+        ld = (size_t)m;
+        __syncthreads();
+    }
 
     for (int j = 0; j < l; ++j) {
-        double* x = Y + (size_t)j * ld;
-        // ||x(j+1:m)||, scaled by a power of two near its largest entry
-        double mx = 0.0;
-        for (int i = j + 1 + tid; i < m; i += kQrThreads) mx = fmax(mx, fabs(x[i]));
-        mx = block_max(mx, red);
-        int e2 = 0;
-        if (mx > 0.0) frexp(mx, &e2);
-        const double isc = ldexp(1.0, -e2);
+        double* x = P + (size_t)j * ld;
         double ssq = 0.0;
-        for (int i = j + 1 + tid; i < m; i += kQrThreads) {
-            const double t = x[i] * isc;
-            ssq = fma(t, t, ssq);
-        }
+        for (int i = j + 1 + tid; i < m; i += kQrThreads) ssq = fma(x[i], x[i], ssq);
         ssq = block_sum(ssq, red);
+        double xnorm = sqrt(ssq);
+        if (!(ssq >= 0x1p-968 && ssq <= 0x1p968)) {
+            // possible under- or overflow: again, scaled by a power of two near the largest entry
+            double mx = 0.0;
+            for (int i = j + 1 + tid; i < m; i += kQrThreads) mx = fmax(mx, fabs(x[i]));
+            mx = block_max(mx, red);
+            xnorm = 0.0;
+            if (mx > 0.0) {
+                int e2 = 0;
+                frexp(mx, &e2);
+                const double isc = ldexp(1.0, -e2);
+                double s2 = 0.0;
+                for (int i = j + 1 + tid; i < m; i += kQrThreads) {
+                    const double t = x[i] * isc;
+                    s2 = fma(t, t, s2);
+                }
+                xnorm = ldexp(sqrt(block_sum(s2, red)), e2);
+            }
+        }
         const double alpha = x[j];
-        const double xnorm = ldexp(sqrt(ssq), e2);
         double tau = 0.0, beta = alpha, scal = 0.0;
         if (xnorm > 0.0) {
             beta = -copysign(hypot(alpha, xnorm), alpha);
@@ -144,56 +185,63 @@ __global__ void __launch_bounds__(kQrThreads) k_house_qr(const QrDesc* __restric
         }
         __syncthreads();   // v complete; every thread has read x[j]
         if (tid == 0) x[j] = beta;
-        if (tau != 0.0) {
-            for (int c = j + 1 + warp; c < l; c += kQrWarps) {
-                double* y = Y + (size_t)c * ld;
-                double dot = 0.0;
-                for (int i = j + lane; i < m; i += 32) dot = fma(v[i], y[i], dot);
-                const double t = tau * warp_sum(dot);
-                for (int i = j + lane; i < m; i += 32) y[i] = fma(-t, v[i], y[i]);
-            }
-        }
+        if (tau != 0.0)
+            for (int c = j + 1 + warp; c < l; c += kQrWarps) reflect_column(v, P + (size_t)c * ld, j, m, tau, lane);
         __syncthreads();
     }
     if (d.R != nullptr) {
         for (int e = tid; e < l * l; e += kQrThreads) {
             const int i = e % l, c = e / l;
-            d.R[(size_t)i + (size_t)c * (size_t)d.ldr] = i <= c ? Y[(size_t)i + (size_t)c * ld] : 0.0;
+            d.R[(size_t)i + (size_t)c * (size_t)d.ldr] = i <= c ? P[(size_t)i + (size_t)c * ld] : 0.0;
         }
     }
     __syncthreads();
     for (int j = l - 1; j >= 0; --j) {
-        double* x = Y + (size_t)j * ld;
+        double* x = P + (size_t)j * ld;
         const double tau = s_tau[j];
         for (int i = j + 1 + tid; i < m; i += kQrThreads) v[i] = x[i];
         if (tid == 0) v[j] = 1.0;
         __syncthreads();
-        if (tau != 0.0) {
-            for (int c = j + 1 + warp; c < l; c += kQrWarps) {
-                double* y = Y + (size_t)c * ld;
-                double dot = 0.0;
-                for (int i = j + lane; i < m; i += 32) dot = fma(v[i], y[i], dot);
-                const double t = tau * warp_sum(dot);
-                for (int i = j + lane; i < m; i += 32) y[i] = fma(-t, v[i], y[i]);
-            }
-        }
+        if (tau != 0.0)
+            for (int c = j + 1 + warp; c < l; c += kQrWarps) reflect_column(v, P + (size_t)c * ld, j, m, tau, lane);
         for (int i = tid; i < m; i += kQrThreads) x[i] = i < j ? 0.0 : (i == j ? 1.0 - tau : -tau * v[i]);
         __syncthreads();
+    }
+    if constexpr (SMEM) {
+        for (int e = tid; e < m * l; e += kQrThreads) d.Y[(size_t)(e % m) + (size_t)(e / m) * (size_t)d.ldy] = P[e];
+    }
+}
+
+// Column pair k of round `round` in the round-robin order of L players
+// (player L-1 fixed, the others rotate); a pair with q >= l is a bye.
+__device__ __forceinline__ void jacobi_pair(int round, int k, int L, int& p, int& q) {
+    p = k == 0 ? round : (round + k) % (L - 1);
+    q = k == 0 ? L - 1 : (round - k + (L - 1)) % (L - 1);
+    if (p > q) {
+        const int t = p;
+        p = q;
+        q = t;
     }
 }
 
 // One-sided Jacobi SVD (Hestenes) of the small matrix M = X Y^T, one CTA per
 // matrix, M and the accumulated rotations W in shared memory.  A sweep
-// visits every column pair once in round-robin order (l/2 disjoint pairs
-// per round, a warp per pair); a pair is rotated when its columns are not
-// orthogonal to working precision, |m_p . m_q| > tol ||m_p|| ||m_q||.  At
-// convergence M W = U~ Sigma with orthogonal columns: sigma_c = ||M(:, c)||,
-// U~(:, c) = M(:, c) / sigma_c (zero when sigma_c = 0).  Columns are written
-// in descending order of sigma.  A sweep limit bounds the iteration; hitting
-// it sets the status word and writes the last iterate.
+// visits every column pair once in round-robin order (l/2 disjoint pairs per
+// round).  A round has three phases, laid out so that no FP64 operation is
+// repeated across lanes (the FP64 pipe is the cost): the three dot products
+// of every pair (T lanes per pair, T the largest power of two with
+// pairs x T <= 32), the rotation of every pair by one lane, and the
+// rotations applied with one lane per (pair, row).  A pair is rotated when
+// |m_p . m_q| > tol ||m_p|| ||m_q||.  At convergence M W = U~ Sigma with
+// orthogonal columns: sigma_c = ||M(:, c)||, U~(:, c) = M(:, c) / sigma_c
+// (zero when sigma_c = 0), written in descending order of sigma.  A sweep
+// limit bounds the iteration; hitting it sets the status word and writes the
+// last iterate.
 __global__ void __launch_bounds__(kSvdThreads) k_jacobi_svd(const SvdDesc* __restrict__ descs,
                                                            int* __restrict__ status) {
     extern __shared__ __align__(16) double sm[];
+    __shared__ double s_abg[3 * kMaxPairs];
+    __shared__ double s_cs[2 * kMaxPairs];
     __shared__ int s_rot[2];
     const SvdDesc d = descs[blockIdx.x];
     const int l = d.l;
@@ -201,7 +249,7 @@ __global__ void __launch_bounds__(kSvdThreads) k_jacobi_svd(const SvdDesc* __res
     double* W = sm + l * l;         // l x l
     double* sg = W + l * l;         // l
     int* perm = reinterpret_cast<int*>(sg + l);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
 
     for (int e = tid; e < l * l; e += kSvdThreads) {
         const int i = e % l, c = e / l;
@@ -217,46 +265,73 @@ __global__ void __launch_bounds__(kSvdThreads) k_jacobi_svd(const SvdDesc* __res
     }
     const double tol = (double)l * 2.220446049250313e-16;   // l x 2^-52
     const int L = (l + 1) & ~1;                              // players, with a bye for odd l
+    const int NP = L / 2;                                    // pairs per round
+    int T = 1;
+    while (2 * T * NP <= 32) T *= 2;
+    const int dot_warps = (NP * T + 31) / 32;
     bool converged = false;
     for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
         const int cur = sweep & 1;
         if (tid == 0) s_rot[cur] = 0;
         __syncthreads();
         for (int round = 0; round < L - 1; ++round) {
-            for (int k = warp; k < L / 2; k += kSvdWarps) {
-                int p = k == 0 ? round : (round + k) % (L - 1);
-                int q = k == 0 ? L - 1 : (round - k + (L - 1)) % (L - 1);
-                if (p > q) {
-                    const int t = p;
-                    p = q;
-                    q = t;
+            if ((tid >> 5) < dot_warps) {           // whole warps, so the shuffles see every lane
+                const int k = tid / T, g = tid % T;
+                int p = 0, q = l;
+                if (k < NP) jacobi_pair(round, k, L, p, q);
+                double a = 0.0, b = 0.0, gm = 0.0;
+                if (q < l) {
+                    for (int i = g; i < l; i += T) {
+                        const double mp = M[i + p * l], mq = M[i + q * l];
+                        a = fma(mp, mp, a);
+                        b = fma(mq, mq, b);
+                        gm = fma(mp, mq, gm);
+                    }
                 }
-                if (q >= l) continue;    // the bye
-                double a = 0.0, b = 0.0, g = 0.0;
-                for (int i = lane; i < l; i += 32) {
-                    const double mp = M[i + p * l], mq = M[i + q * l];
-                    a = fma(mp, mp, a);
-                    b = fma(mq, mq, b);
-                    g = fma(mp, mq, g);
+                for (int o = T >> 1; o > 0; o >>= 1) {
+                    a += __shfl_xor_sync(0xffffffffu, a, o);
+                    b += __shfl_xor_sync(0xffffffffu, b, o);
+                    gm += __shfl_xor_sync(0xffffffffu, gm, o);
                 }
-                a = warp_sum(a);
-                b = warp_sum(b);
-                g = warp_sum(g);
-                if (g != 0.0 && fabs(g) > tol * sqrt(a) * sqrt(b)) {
+                if (g == 0 && k < NP) {
+                    s_abg[3 * k] = a;
+                    s_abg[3 * k + 1] = b;
+                    s_abg[3 * k + 2] = gm;
+                }
+            }
+            __syncthreads();
+            if (tid < NP) {
+                int p, q;
+                jacobi_pair(round, tid, L, p, q);
+                double c = 1.0, s = 0.0;
+                const double a = s_abg[3 * tid], b = s_abg[3 * tid + 1], g = s_abg[3 * tid + 2];
+                if (q < l && g != 0.0 && fabs(g) > tol * sqrt(a) * sqrt(b)) {
                     // t = tan(theta) of the rotation that makes the pair orthogonal
                     const double zeta = (b - a) / (2.0 * g);
-                    const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-                    const double c = 1.0 / sqrt(fma(t, t, 1.0)), s = c * t;
-                    for (int i = lane; i < l; i += 32) {
-                        const double mp = M[i + p * l], mq = M[i + q * l];
-                        M[i + p * l] = c * mp - s * mq;
-                        M[i + q * l] = s * mp + c * mq;
-                        const double wp = W[i + p * l], wq = W[i + q * l];
-                        W[i + p * l] = c * wp - s * wq;
-                        W[i + q * l] = s * wp + c * wq;
-                    }
-                    if (lane == 0) s_rot[cur] = 1;
+                    const double az = fabs(zeta);
+                    const double root = az < 1e100 ? sqrt(fma(az, az, 1.0)) : az;
+                    const double t = copysign(1.0 / (az + root), zeta);
+                    c = 1.0 / sqrt(fma(t, t, 1.0));
+                    s = c * t;
+                    if (s != 0.0) s_rot[cur] = 1;
                 }
+                s_cs[2 * tid] = c;
+                s_cs[2 * tid + 1] = s;
+            }
+            __syncthreads();
+            for (int e = tid; e < NP * l; e += kSvdThreads) {
+                const int k = e / l, i = e % l;
+                const double s = s_cs[2 * k + 1];
+                if (s == 0.0) continue;
+                const double c = s_cs[2 * k];
+                int p, q;
+                jacobi_pair(round, k, L, p, q);
+                const double mp = M[i + p * l], mq = M[i + q * l];
+                M[i + p * l] = c * mp - s * mq;
+                M[i + q * l] = s * mp + c * mq;
+                const double wp = W[i + p * l], wq = W[i + q * l];
+                W[i + p * l] = c * wp - s * wq;
+                W[i + q * l] = s * wp + c * wq;
             }
             __syncthreads();
         }
@@ -457,10 +532,33 @@ struct Step {
     int count;
     size_t smem;
     lrb_plan* g;
+    bool panel = false;   // QR: the panel is staged in shared memory
 };
 
-lrb_status set_smem_limits(size_t qr_smem, size_t svd_smem_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(k_house_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qr_smem);
+// Shared memory a CTA may take beyond the kernels' static arrays.
+size_t dyn_smem_limit(int device) {
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) return 48 << 10;
+    return (size_t)optin - 2048;
+}
+
+// A QR step over `count` matrices of at most rows x cols: the shared-memory
+// panel form when rows x (cols + 1) doubles fit, else the in-place form.
+Step qr_step(size_t off, int count, int rows, int cols, size_t limit) {
+    const size_t panel = 8 * (size_t)rows * (cols + 1) + 16;
+    Step st{Step::kQr, off, count, 8 * (size_t)rows + 16, nullptr, false};
+    if (panel <= limit) {
+        st.smem = panel;
+        st.panel = true;
+    }
+    return st;
+}
+
+lrb_status set_smem_limits(size_t limit, size_t svd_smem_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(k_house_qr<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_house_qr<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(8 * LRB_LR_MAX_ROWS + 16));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_jacobi_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)svd_smem_bytes);
     return e == cudaSuccess ? LRB_OK : cuda_err(e, "kernel shared-memory limit");
@@ -486,7 +584,10 @@ lrb_status finish(LrPlan* p, Uploader& up, const std::vector<Step>& steps) {
                 le = enqueue_fp64_plan(s.g, p->cap);
                 break;
             case Step::kQr:
-                k_house_qr<<<s.count, kQrThreads, s.smem, p->cap>>>(at<QrDesc>(p->dmem, s.off));
+                if (s.panel)
+                    k_house_qr<true><<<s.count, kQrThreads, s.smem, p->cap>>>(at<QrDesc>(p->dmem, s.off));
+                else
+                    k_house_qr<false><<<s.count, kQrThreads, s.smem, p->cap>>>(at<QrDesc>(p->dmem, s.off));
                 le = cudaGetLastError();
                 break;
             case Step::kSvd:
@@ -541,7 +642,7 @@ lrb_status create_rsvd(lrb_handle* h, const lrb_rsvd_desc* d, size_t count, int 
     if (q < 0 || q > 8) return fail0(LRB_ERR_INVALID, "power_iters must be 0..8");
     std::vector<Rng> rng;
     double flops = 0, bytes = 0;
-    int maxrows = 1, maxl = 1;
+    int maxl = 1, maxm = 1, maxn = 1;
     for (size_t e = 0; e < count; ++e) {
         const lrb_rsvd_desc& x = d[e];
         const lrb_lr_block& b = x.out;
@@ -557,7 +658,8 @@ lrb_status create_rsvd(lrb_handle* h, const lrb_rsvd_desc* d, size_t count, int 
         const double m = b.m, n = b.n, l = x.l, r = b.r;
         flops += 2.0 * m * n * l * (2 + 2 * q) + (1 + q) * (qr_flops(m, l) + qr_flops(n, l)) + 2.0 * (m + n) * l * r;
         bytes += 8.0 * (m * n + n * l + m * r + r + r * n);
-        maxrows = std::max({maxrows, b.m, b.n});
+        maxm = std::max(maxm, b.m);
+        maxn = std::max(maxn, b.n);
         maxl = std::max(maxl, x.l);
     }
     if (overlaps(rng)) {
@@ -572,7 +674,8 @@ lrb_status create_rsvd(lrb_handle* h, const lrb_rsvd_desc* d, size_t count, int 
         destroy(p);
         return s;
     };
-    lrb_status s = set_smem_limits(8 * (size_t)maxrows + 16, svd_smem(maxl));
+    const size_t limit = dyn_smem_limit(p->device);
+    lrb_status s = set_smem_limits(limit, svd_smem(maxl));
     if (s != LRB_OK) return bail(s);
 
     Bump bump;
@@ -618,18 +721,17 @@ lrb_status create_rsvd(lrb_handle* h, const lrb_rsvd_desc* d, size_t count, int 
     const size_t oZR = up.add(qZR.data(), sizeof(QrDesc) * count);
     const size_t oS = up.add(sv.data(), sizeof(SvdDesc) * count);
     const int c = (int)count;
-    const size_t qm = 8 * (size_t)maxrows + 16;
     std::vector<Step> steps;
     steps.push_back({Step::kGemm, 0, 0, 0, pAO});
-    steps.push_back({Step::kQr, oY, c, qm, nullptr});
+    steps.push_back(qr_step(oY, c, maxm, maxl, limit));
     for (int it = 0; it < q; ++it) {
         steps.push_back({Step::kGemm, 0, 0, 0, pATY});
-        steps.push_back({Step::kQr, oZ, c, qm, nullptr});
+        steps.push_back(qr_step(oZ, c, maxn, maxl, limit));
         steps.push_back({Step::kGemm, 0, 0, 0, pAZ});
-        steps.push_back({Step::kQr, oY, c, qm, nullptr});
+        steps.push_back(qr_step(oY, c, maxm, maxl, limit));
     }
     steps.push_back({Step::kGemm, 0, 0, 0, pATY});
-    steps.push_back({Step::kQr, oZR, c, qm, nullptr});
+    steps.push_back(qr_step(oZR, c, maxn, maxl, limit));
     steps.push_back({Step::kSvd, oS, c, svd_smem(maxl), nullptr});
     steps.push_back({Step::kGemm, 0, 0, 0, pU});
     steps.push_back({Step::kGemm, 0, 0, 0, pV});
@@ -716,7 +818,7 @@ lrb_status create_round_add(lrb_handle* h, const lrb_round_add_desc* d, size_t c
     if (count == 0 || count > 0x7fffffffull) return failv(LRB_ERR_INVALID, "count %zu out of range", count);
     std::vector<Rng> rng;
     double flops = 0, bytes = 0;
-    int maxrows = 1, maxl = 1;
+    int maxl = 1, maxm = 1, maxn = 1;
     for (size_t e = 0; e < count; ++e) {
         const lrb_round_add_desc& x = d[e];
         lrb_status s;
@@ -732,7 +834,8 @@ lrb_status create_round_add(lrb_handle* h, const lrb_round_add_desc* d, size_t c
         const double M = m, N = n, L = lc, r = x.out.r;
         flops += qr_flops(M, L) + qr_flops(N, L) + 2.0 * L * L * L + 2.0 * (M + N) * L * r;
         bytes += 8.0 * ((M + N + 1) * L + (M + N + 1) * r);
-        maxrows = std::max({maxrows, m, n});
+        maxm = std::max(maxm, m);
+        maxn = std::max(maxn, n);
         maxl = std::max(maxl, lc);
     }
     if (overlaps(rng)) {
@@ -747,7 +850,8 @@ lrb_status create_round_add(lrb_handle* h, const lrb_round_add_desc* d, size_t c
         destroy(p);
         return s;
     };
-    lrb_status s = set_smem_limits(8 * (size_t)maxrows + 16, svd_smem(maxl));
+    const size_t limit = dyn_smem_limit(p->device);
+    lrb_status s = set_smem_limits(limit, svd_smem(maxl));
     if (s != LRB_OK) return bail(s);
     Bump bump;
     struct Off {
@@ -786,10 +890,12 @@ lrb_status create_round_add(lrb_handle* h, const lrb_round_add_desc* d, size_t c
     const size_t oQ2 = up.add(q2.data(), sizeof(QrDesc) * count);
     const size_t oS = up.add(sv.data(), sizeof(SvdDesc) * count);
     const int c = (int)count;
-    const size_t qm = 8 * (size_t)maxrows + 16;
-    std::vector<Step> steps{{Step::kPack, oPU, c, 0, nullptr},  {Step::kPackT, oPV, c, 0, nullptr},
-                            {Step::kQr, oQ1, c, qm, nullptr},    {Step::kQr, oQ2, c, qm, nullptr},
-                            {Step::kSvd, oS, c, svd_smem(maxl), nullptr}, {Step::kGemm, 0, 0, 0, pU},
+    std::vector<Step> steps{{Step::kPack, oPU, c, 0, nullptr},
+                            {Step::kPackT, oPV, c, 0, nullptr},
+                            qr_step(oQ1, c, maxm, maxl, limit),
+                            qr_step(oQ2, c, maxn, maxl, limit),
+                            {Step::kSvd, oS, c, svd_smem(maxl), nullptr},
+                            {Step::kGemm, 0, 0, 0, pU},
                             {Step::kGemm, 0, 0, 0, pV}};
     if ((s = finish(p, up, steps)) != LRB_OK) return bail(s);
     std::memset(info, 0, sizeof(*info));
