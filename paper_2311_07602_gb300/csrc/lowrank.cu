@@ -73,24 +73,38 @@ __device__ __forceinline__ double warp_max(double v) {
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
-// Every thread receives the block's sum (warp partials added in warp order).
+// Every thread receives the block's sum: warp partials, then warp 0 adds the
+// kQrWarps partials (a butterfly over 16 lanes) and broadcasts through
+// red[kQrWarps].  Only warp 0 spends FP64 instructions on the second level:
+// on this GPU a warp-wide FP64 add costs the FP64 pipe the same whether one
+// warp or all of them need the result.
 __device__ double block_sum(double v, double* red) {
     v = warp_sum(v);
     __syncthreads();
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
-    double t = 0.0;
-    for (int w = 0; w < kQrWarps; ++w) t += red[w];
-    return t;
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < kQrWarps ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = kQrWarps / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) red[kQrWarps] = t;
+    }
+    __syncthreads();
+    return red[kQrWarps];
 }
 __device__ double block_max(double v, double* red) {
     v = warp_max(v);
     __syncthreads();
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
-    double t = 0.0;
-    for (int w = 0; w < kQrWarps; ++w) t = fmax(t, red[w]);
-    return t;
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < kQrWarps ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = kQrWarps / 2; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
+        if (threadIdx.x == 0) red[kQrWarps] = t;
+    }
+    __syncthreads();
+    return red[kQrWarps];
 }
 
 // One warp applies H = I - tau v v^T to rows [j, m) of column y:
@@ -128,8 +142,9 @@ __device__ __forceinline__ void reflect_column(const double* __restrict__ v, dou
 template <bool SMEM>
 __global__ void __launch_bounds__(kQrThreads) k_house_qr(const QrDesc* __restrict__ descs) {
     extern __shared__ __align__(16) double sm[];
-    __shared__ double red[kQrWarps];
+    __shared__ double red[kQrWarps + 1];
     __shared__ double s_tau[LRB_LR_MAX_L];
+    __shared__ double s_par[3];
     const QrDesc d = descs[blockIdx.x];
     const int m = d.rows, l = d.cols;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -148,15 +163,14 @@ __global__ void __launch_bounds__(kQrThreads) k_house_qr(const QrDesc* __restric
         double ssq = 0.0;
         for (int i = j + 1 + tid; i < m; i += kQrThreads) ssq = fma(x[i], x[i], ssq);
         ssq = block_sum(ssq, red);
-        double xnorm = sqrt(ssq);
+        int e2 = 0;                           // ||x(j+1:m)|| = 2^e2 sqrt(ssq)
         if (!(ssq >= 0x1p-968 && ssq <= 0x1p968)) {
             // possible under- or overflow: again, scaled by a power of two near the largest entry
             double mx = 0.0;
             for (int i = j + 1 + tid; i < m; i += kQrThreads) mx = fmax(mx, fabs(x[i]));
             mx = block_max(mx, red);
-            xnorm = 0.0;
+            ssq = 0.0;
             if (mx > 0.0) {
-                int e2 = 0;
                 frexp(mx, &e2);
                 const double isc = ldexp(1.0, -e2);
                 double s2 = 0.0;
@@ -164,27 +178,37 @@ __global__ void __launch_bounds__(kQrThreads) k_house_qr(const QrDesc* __restric
                     const double t = x[i] * isc;
                     s2 = fma(t, t, s2);
                 }
-                xnorm = ldexp(sqrt(block_sum(s2, red)), e2);
+                ssq = block_sum(s2, red);
             }
         }
-        const double alpha = x[j];
-        double tau = 0.0, beta = alpha, scal = 0.0;
-        if (xnorm > 0.0) {
-            beta = -copysign(hypot(alpha, xnorm), alpha);
-            tau = (beta - alpha) / beta;
-            scal = 1.0 / (alpha - beta);
+        // the reflector's scalars, by warp 0 alone (a warp-wide FP64 operation
+        // costs the pipe the same for one lane as for 32): s_par = {tau, beta, scal}
+        if (warp == 0) {
+            const double alpha = x[j];
+            const double xnorm = ldexp(sqrt(ssq), e2);
+            double tau = 0.0, beta = alpha, scal = 0.0;
+            if (xnorm > 0.0) {
+                beta = -copysign(hypot(alpha, xnorm), alpha);
+                tau = (beta - alpha) / beta;
+                scal = 1.0 / (alpha - beta);
+            }
+            if (lane == 0) {
+                s_par[0] = tau;
+                s_par[1] = beta;
+                s_par[2] = scal;
+                s_tau[j] = tau;
+                v[j] = 1.0;
+            }
         }
+        __syncthreads();
+        const double tau = s_par[0], scal = s_par[2];
         for (int i = j + 1 + tid; i < m; i += kQrThreads) {
             const double t = x[i] * scal;
             x[i] = t;
             v[i] = t;
         }
-        if (tid == 0) {
-            v[j] = 1.0;
-            s_tau[j] = tau;
-        }
-        __syncthreads();   // v complete; every thread has read x[j]
-        if (tid == 0) x[j] = beta;
+        __syncthreads();   // v complete
+        if (tid == 0) x[j] = s_par[1];
         if (tau != 0.0)
             for (int c = j + 1 + warp; c < l; c += kQrWarps) reflect_column(v, P + (size_t)c * ld, j, m, tau, lane);
         __syncthreads();
