@@ -44,8 +44,8 @@ DFMA_LANES_PER_SM_CLK = 2          # FP64 FMA lanes per SM per clock on GB300 (1
 # DRAM bytes per algorithmic byte of k_persistent, from the ncu capture in
 # profiles/k_persistent_fp64_uniform_sweep.md (small case of the same sweep),
 # valid while fp64_tiles.cu has the SHA-256 prefix below.
-TRAFFIC_PER_ALG_BYTE = 2.0566e9 / 2.018344960e9
-TRAFFIC_SOURCE_SHA = "8a8eddd9eb6fc526"
+TRAFFIC_PER_ALG_BYTE = 2.067912e9 / 2.018344960e9
+TRAFFIC_SOURCE_SHA = "c86a6ad4ee65ca25"
 
 
 def dist_env():

@@ -73,62 +73,72 @@ __device__ __forceinline__ double warp_max(double v) {
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
-// Every thread receives the block's sum: warp partials, then warp 0 adds the
-// kQrWarps partials (a butterfly over 16 lanes) and broadcasts through
-// red[kQrWarps].  Only warp 0 spends FP64 instructions on the second level:
-// on this GPU a warp-wide FP64 add costs the FP64 pipe the same whether one
-// warp or all of them need the result.
+// Every thread receives the block's sum.  The threads' partials go to shared
+// memory and warp 0 alone adds them (16 per lane, then a butterfly), so the
+// sum costs ~21 warp-wide FP64 adds instead of 5 per warp: on this GPU a
+// warp-wide FP64 add costs the FP64 pipe the same for any number of active
+// lanes.  red holds kQrThreads + 1 doubles; the result is red[kQrThreads].
 __device__ double block_sum(double v, double* red) {
-    v = warp_sum(v);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();                 // the previous result has been read
+    red[threadIdx.x] = v;
     __syncthreads();
     if (threadIdx.x < 32) {
-        double t = threadIdx.x < kQrWarps ? red[threadIdx.x] : 0.0;
+        double t = 0.0;
 #pragma unroll
-        for (int o = kQrWarps / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (threadIdx.x == 0) red[kQrWarps] = t;
+        for (int k = 0; k < kQrWarps; ++k) t += red[threadIdx.x + 32 * k];
+        t = warp_sum(t);
+        if (threadIdx.x == 0) red[kQrThreads] = t;
     }
     __syncthreads();
-    return red[kQrWarps];
+    return red[kQrThreads];
 }
 __device__ double block_max(double v, double* red) {
-    v = warp_max(v);
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    red[threadIdx.x] = v;
     __syncthreads();
     if (threadIdx.x < 32) {
-        double t = threadIdx.x < kQrWarps ? red[threadIdx.x] : 0.0;
+        double t = 0.0;
 #pragma unroll
-        for (int o = kQrWarps / 2; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
-        if (threadIdx.x == 0) red[kQrWarps] = t;
+        for (int k = 0; k < kQrWarps; ++k) t = fmax(t, red[threadIdx.x + 32 * k]);
+        t = warp_max(t);
+        if (threadIdx.x == 0) red[kQrThreads] = t;
     }
     __syncthreads();
-    return red[kQrWarps];
+    return red[kQrThreads];
 }
 
 // One warp applies H = I - tau v v^T to rows [j, m) of column y:
-// y <- y - tau (v^T y) v, with four independent partial sums so that the
-// loads of a column are in flight together.
+// y <- y - tau (v^T y) v.  Trip counts are the same for every lane (a lane
+// past the end is predicated off in the last step only), and four
+// independent partial sums keep a column's loads in flight together.
 __device__ __forceinline__ void reflect_column(const double* __restrict__ v, double* y, int j, int m, double tau,
                                                int lane) {
     double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
-    int i = j + lane;
-    for (; i + 96 < m; i += 128) {
+    int base = j;
+    for (; base + 128 <= m; base += 128) {
+        const int i = base + lane;
         d0 = fma(v[i], y[i], d0);
         d1 = fma(v[i + 32], y[i + 32], d1);
         d2 = fma(v[i + 64], y[i + 64], d2);
         d3 = fma(v[i + 96], y[i + 96], d3);
     }
-    for (; i < m; i += 32) d0 = fma(v[i], y[i], d0);
+    const int tail = base;
+    for (; base < m; base += 32) {
+        const int i = base + lane;
+        if (i < m) d0 = fma(v[i], y[i], d0);
+    }
     const double t = tau * warp_sum((d0 + d1) + (d2 + d3));
-    for (i = j + lane; i + 96 < m; i += 128) {
+    for (base = j; base + 128 <= m; base += 128) {
+        const int i = base + lane;
         y[i] = fma(-t, v[i], y[i]);
         y[i + 32] = fma(-t, v[i + 32], y[i + 32]);
         y[i + 64] = fma(-t, v[i + 64], y[i + 64]);
         y[i + 96] = fma(-t, v[i + 96], y[i + 96]);
     }
-    for (; i < m; i += 32) y[i] = fma(-t, v[i], y[i]);
+    for (base = tail; base < m; base += 32) {
+        const int i = base + lane;
+        if (i < m) y[i] = fma(-t, v[i], y[i]);
+    }
 }
 
 // Householder QR of one tall matrix per CTA (rows >= cols), the reflectors
@@ -140,9 +150,9 @@ __device__ __forceinline__ void reflect_column(const double* __restrict__ v, dou
 // Q.  SMEM: the whole panel is staged in shared memory (rows x (cols + 1)
 // doubles with v), else it is worked on in place in global memory (L2).
 template <bool SMEM>
-__global__ void __launch_bounds__(kQrThreads) k_house_qr(const QrDesc* __restrict__ descs) {
+__global__ void __launch_bounds__(kQrThreads, 1) k_house_qr(const QrDesc* __restrict__ descs) {
     extern __shared__ __align__(16) double sm[];
-    __shared__ double red[kQrWarps + 1];
+    __shared__ double red[kQrThreads + 1];
     __shared__ double s_tau[LRB_LR_MAX_L];
     __shared__ double s_par[3];
     const QrDesc d = descs[blockIdx.x];
@@ -559,11 +569,14 @@ struct Step {
     bool panel = false;   // QR: the panel is staged in shared memory
 };
 
-// Shared memory a CTA may take beyond the kernels' static arrays.
+// Dynamic shared memory a QR CTA may take beyond its static arrays.
 size_t dyn_smem_limit(int device) {
     int optin = 0;
-    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) return 48 << 10;
-    return (size_t)optin - 2048;
+    cudaFuncAttributes fa;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, k_house_qr<true>) != cudaSuccess)
+        return 0;
+    return (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
 }
 
 // A QR step over `count` matrices of at most rows x cols: the shared-memory
