@@ -262,6 +262,7 @@ struct lrb_plan {
     int lr_kind = 0;                   // 0: none, 1: fused, 2: unfused (three batched products)
     LrDesc* d_lr = nullptr;
     int lr_count = 0;
+    int lr_rmax = 0;                   // largest rank of any block (sizes the fused kernel)
     void* lr_work = nullptr;           // unfused: C_temp and E_temp of every block
     size_t lr_work_bytes = 0;
     lrb_plan* lr_stage[3] = {nullptr, nullptr, nullptr};
@@ -735,7 +736,7 @@ lrb_status lrb_launch(lrb_plan* p, void* stream) {
         return e == cudaSuccess ? LRB_OK : cuda_fail(e, "low-rank plan launch");
     }
     if (p->lr_kind == 1) {
-        cudaError_t e = launch_lr_chain(p->d_lr, p->lr_count, s);
+        cudaError_t e = launch_lr_chain(p->d_lr, p->lr_count, p->lr_rmax, s);
         return e == cudaSuccess ? LRB_OK : cuda_fail(e, "low-rank chain launch");
     }
     if (p->lr_kind == 2) {
@@ -1083,6 +1084,7 @@ lrb_status lrb_lr_plan_create(lrb_handle* h, const lrb_lr_desc* d, size_t count,
     p->h = h;
     p->lr_kind = fused ? 1 : 2;
     p->lr_count = (int)count;
+    for (size_t e = 0; e < count; ++e) p->lr_rmax = std::max({p->lr_rmax, (int)d[e].ra, (int)d[e].rb});
     p->info.entries = (int64_t)count;
     p->info.flops = flops;
     p->info.alg_bytes = bytes;

@@ -11,10 +11,15 @@
 // exactly one DFMA per multiply-add of the chain:
 //   step 1  C_temp = A_{V^T} B_U: 2x2 register micro-tiles; the threads left
 //           over split k, and the k-groups are summed in a fixed order;
-//           k is staged in steps of 32 with cp.async double buffering;
+//           k is staged with cp.async double buffering;
 //   step 2  E_temp = A_X C_temp and step 3 G = E_temp B_X from shared
 //           memory (A_X, B_X read through the read-only cache).
-// Ranks up to 64 (the paper's sweep uses 8..32).
+// Ranks up to 64 (the paper's sweep uses 8..32).  A plan sizes the kernel for
+// its largest rank R: the micro-tile passes per thread (a template argument)
+// and the staging area (KL k-rows of both operands per buffer, KL x R
+// doubles, with KL larger for small R) -- so that rank-8 and rank-16 plans
+// keep several times more CTAs per SM than rank-64 plans, which is what
+// hides the load latency of blocks this small.
 #include <algorithm>
 
 #include "lrb_internal.h"
@@ -23,34 +28,37 @@ namespace lrb {
 namespace {
 
 constexpr int kLT = 128;     // threads per CTA
-constexpr int kLK = 32;      // k-step at rank 64
 constexpr int kRmax = 64;
-constexpr int kStage = kLK * kRmax;   // doubles per operand and buffer: the k-step is kStage / R
 
 __device__ __forceinline__ void cpa8(double* dst, const double* src, bool pred) {
     const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(dst));
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(src), "r"(pred ? 8 : 0) : "memory");
 }
 
-__global__ void __launch_bounds__(kLT) k_lr_chain(const LrDesc* __restrict__ descs) {
+// stage: doubles per operand and buffer (>= R_plan^2 / 2, so that C_temp and
+// E_temp fit in the staging area afterwards); PASSES: 2x2 micro-tiles per
+// thread when a block has more than 128 of them.
+template <int PASSES>
+__global__ void __launch_bounds__(kLT, PASSES <= 2 ? 8 : PASSES == 4 ? 6 : 3) k_lr_chain(const LrDesc* __restrict__ descs,
+                                                                                  int stage) {
     extern __shared__ __align__(16) double sm[];
     const LrDesc d = descs[blockIdx.x];
     const int ra = d.ra, rb = d.rb, k = d.k;
     const int tid = threadIdx.x;
     // step-1 staging: [2][KL][R] of A_{V^T} columns and [2][KL][R] of B_U rows,
-    // R = max(ra, rb) rounded up to even, KL = kStage / R (k-step grows as the
+    // R = max(ra, rb) rounded up to even, KL = stage / R (k-step grows as the
     // rank shrinks, so every k-step carries the same work)
     const int R = ((ra > rb ? ra : rb) + 1) & ~1;
-    const int KL = kStage / R;
+    const int KL = stage / R;
     double* sA = sm;
-    double* sB = sm + 2 * kStage;
-    double* red = sm + 4 * kStage;             // [KS][4 P] partial sums
+    double* sB = sm + 2 * stage;
+    double* red = sm + 4 * stage;              // [KS][4 P] partial sums
     const int mt = (ra + 1) / 2, nt = (rb + 1) / 2;
     const int P = mt * nt;                      // 2x2 micro-tiles
     const int KS = P >= kLT ? 1 : kLT / P;      // k-groups
     const int passes = (P + kLT - 1) / kLT;     // micro-tiles per thread when P > 128
 
-    auto stage = [&](int kt, int buf) {
+    auto stage_in = [&](int kt, int buf) {
         const int k0 = kt * KL;
         const int kl = min(KL, k - k0);
         for (int e = tid; e < KL * ra; e += kLT) {
@@ -67,9 +75,9 @@ __global__ void __launch_bounds__(kLT) k_lr_chain(const LrDesc* __restrict__ des
     };
 
     // ---- step 1 ----
-    double acc[8][4];   // up to 8 micro-tiles per thread (rank 64) x 2x2
+    double acc[PASSES][4];
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
+    for (int a = 0; a < PASSES; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
     const int my_tile = tid % (P < kLT ? P : kLT);
@@ -77,11 +85,11 @@ __global__ void __launch_bounds__(kLT) k_lr_chain(const LrDesc* __restrict__ des
     const bool active = P >= kLT || tid < P * KS;
     const int nk = (k + KL - 1) / KL;
     // (with KS > 1, KS * P <= 128, so the reduction area holds 4 * 128 doubles)
-    stage(0, 0);
+    stage_in(0, 0);
     for (int kt = 0; kt < nk; ++kt) {
         const int buf = kt & 1;
         if (kt + 1 < nk) {
-            stage(kt + 1, buf ^ 1);
+            stage_in(kt + 1, buf ^ 1);
             asm volatile("cp.async.wait_group 1;\n" ::: "memory");
         } else {
             asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -90,7 +98,7 @@ __global__ void __launch_bounds__(kLT) k_lr_chain(const LrDesc* __restrict__ des
         const int kl = min(KL, k - kt * KL);
         if (active) {
 #pragma unroll
-            for (int pass = 0; pass < 8; ++pass) {
+            for (int pass = 0; pass < PASSES; ++pass) {
                 const int t = my_tile + pass * kLT;
                 if (pass >= passes || t >= P) break;
                 const int i0 = 2 * (t % mt), j0 = 2 * (t / mt);
@@ -117,10 +125,10 @@ __global__ void __launch_bounds__(kLT) k_lr_chain(const LrDesc* __restrict__ des
     }
     // k-groups -> C_temp (fixed order), into shared memory (staging is free now)
     double* Ct = sm;                       // ra x rb, column-major, ld ra
-    double* Et = sm + kRmax * kRmax;       // ra x rb
+    double* Et = sm + 2 * stage;           // ra x rb
     if (KS == 1) {
 #pragma unroll
-        for (int pass = 0; pass < 8; ++pass) {
+        for (int pass = 0; pass < PASSES; ++pass) {
             const int t = my_tile + pass * kLT;
             if (!active || pass >= passes || t >= P) break;   // (64 < P < 128 leaves threads idle)
             const int i0 = 2 * (t % mt), j0 = 2 * (t / mt);
@@ -132,15 +140,11 @@ __global__ void __launch_bounds__(kLT) k_lr_chain(const LrDesc* __restrict__ des
             }
         }
     } else if (active) {
-        {
-            const int pass = 0;   // with KS > 1, P < 128: one micro-tile per thread
-            const int t = my_tile;
-            double* r = red + (size_t)kg * (4 * P) + 4 * t;
-            r[0] = acc[pass][0];
-            r[1] = acc[pass][1];
-            r[2] = acc[pass][2];
-            r[3] = acc[pass][3];
-        }
+        double* r = red + (size_t)kg * (4 * P) + 4 * my_tile;   // with KS > 1, P < 128: one micro-tile per thread
+        r[0] = acc[0][0];
+        r[1] = acc[0][1];
+        r[2] = acc[0][2];
+        r[3] = acc[0][3];
     }
     __syncthreads();
     for (int t = tid; KS > 1 && t < P; t += kLT) {
@@ -174,22 +178,47 @@ __global__ void __launch_bounds__(kLT) k_lr_chain(const LrDesc* __restrict__ des
     }
 }
 
+// Kernel configuration for a plan whose largest rank is rmax: staging KL x R
+// with KL = max(32, 768 / R) (R = rmax rounded up to even), passes from the
+// micro-tile count.
+struct ChainCfg {
+    int stage, passes;
+};
+ChainCfg chain_cfg(int rmax) {
+    const int R = std::max(2, (rmax + 1) & ~1);
+    const int KL = std::max(32, 768 / R);
+    const int P = ((rmax + 1) / 2) * ((rmax + 1) / 2);
+    const int pass = (P + kLT - 1) / kLT;
+    return ChainCfg{KL * R, pass <= 1 ? 1 : pass <= 2 ? 2 : pass <= 4 ? 4 : 8};
+}
+
+template <int PASSES>
+cudaError_t launch_chain(const LrDesc* d_descs, int count, int stage, cudaStream_t s) {
+    const size_t smem = lr_chain_smem_bytes_for(stage);
+    cudaError_t e = cudaFuncSetAttribute(k_lr_chain<PASSES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (count <= 0) return cudaSuccess;
+    k_lr_chain<PASSES><<<count, kLT, smem, s>>>(d_descs, stage);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
-size_t lr_chain_smem_bytes() {
-    // staging 4 kStage doubles (reused for C_temp and E_temp) + reduction 4 kLT doubles
-    return 8 * (size_t)(4 * kStage + 4 * kLT + 8);
+size_t lr_chain_smem_bytes_for(int stage) {
+    // staging 4 stage doubles (reused for C_temp and E_temp) + reduction 4 kLT doubles
+    return 8 * (size_t)(4 * stage + 4 * kLT + 8);
 }
 
 int lr_chain_max_rank() { return kRmax; }
 
-cudaError_t launch_lr_chain(const LrDesc* d_descs, int count, cudaStream_t s) {
-    const size_t smem = lr_chain_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(k_lr_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    if (count <= 0) return cudaSuccess;
-    k_lr_chain<<<count, kLT, smem, s>>>(d_descs);
-    return cudaGetLastError();
+cudaError_t launch_lr_chain(const LrDesc* d_descs, int count, int rmax, cudaStream_t s) {
+    const ChainCfg c = chain_cfg(rmax);
+    switch (c.passes) {
+        case 1: return launch_chain<1>(d_descs, count, c.stage, s);
+        case 2: return launch_chain<2>(d_descs, count, c.stage, s);
+        case 4: return launch_chain<4>(d_descs, count, c.stage, s);
+        default: return launch_chain<8>(d_descs, count, c.stage, s);
+    }
 }
 
 }  // namespace lrb

@@ -74,9 +74,10 @@ int persistent_blocks_per_sm(int set = 1);
 int variant_set(int v);
 
 // Fused low-rank chain (lr_chain.cu).
-size_t lr_chain_smem_bytes();
+// rmax: the plan's largest rank (sizes the kernel's registers and staging).
+size_t lr_chain_smem_bytes_for(int stage);
 int lr_chain_max_rank();
-cudaError_t launch_lr_chain(const LrDesc* d_descs, int count, cudaStream_t s);
+cudaError_t launch_lr_chain(const LrDesc* d_descs, int count, int rmax, cudaStream_t s);
 cudaError_t launch_lr_zero(const LrDesc* d_descs, int count, cudaStream_t s);
 
 // Sets the calling thread's lrb_last_error() message (api.cu).
