@@ -14,9 +14,11 @@ Three batched calls of the library, nothing else on the path:
      written into a per-row stack T_i = [T_ij]_j ((nb-1) r x nrhs);
   3. Y_i += [U_ij]_j T_i, one product per block row with k = (nb-1) r, the
      U blocks of a row stored side by side.
-Step 3 gives every block row one entry, so no two entries write the same
-part of Y.  Y's blocks interleave in memory (ld = N), so the byte-range alias
-check, which is conservative, is switched off for steps 1 and 3.
+Steps 1 and 2 touch disjoint outputs (Y and the stacks T) and run on two
+streams at once; step 3 waits for both.  Step 3 gives every block row one
+entry, so no two entries write the same part of Y.  Y's blocks interleave in
+memory (ld = N), so the byte-range alias check, which is conservative, is
+switched off for steps 1 and 3.
 """
 from __future__ import annotations
 
@@ -102,14 +104,25 @@ class BLRMatVec:
         d3["B"] = np.uint64(t0) + 8 * i * np.uint64((nb - 1) * r * nrhs)
         d3["C"] = np.uint64(y0) + 8 * i * np.uint64(b)
         d3["m"], d3["n"], d3["k"], d3["lda"], d3["ldb"], d3["ldc"] = b, nrhs, (nb - 1) * r, b, (nb - 1) * r, N
+        self.side = None
         self.p1 = handle.plan(d1, check_alias=False, use_graph=True)
         self.p2 = L.Plan(handle, d2, lr_fused=fused)
         self.p3 = handle.plan(d3, check_alias=False, use_graph=True)
 
     def run(self, stream=None):
-        self.p1.launch(stream)
-        self.p2.launch(stream)
-        self.p3.launch(stream)
+        # steps 1 and 2 write different buffers (Y, T), so they run concurrently:
+        # the chains fill the SMs the diagonal product's last wave leaves idle
+        s = stream if stream is not None else torch.cuda.current_stream()
+        if self.side is None:
+            self.side = torch.cuda.Stream(device=s.device)
+            self.ev_fork, self.ev_join = torch.cuda.Event(), torch.cuda.Event()
+        self.ev_fork.record(s)
+        self.side.wait_event(self.ev_fork)
+        self.p2.launch(self.side)
+        self.p1.launch(s)
+        self.ev_join.record(self.side)
+        s.wait_event(self.ev_join)
+        self.p3.launch(s)
 
     def close(self):
         for p in (self.p1, self.p2, self.p3):

@@ -634,6 +634,20 @@ lrb_status lrb_plan_create(lrb_handle* h, const lrb_gemm_desc* host_descs, size_
     }
     std::vector<Item> items;
     make_tiles(host_descs, count, var, items);
+    if (o.force_variant < 0 && items.size() < 2 * (size_t)h->sms * (size_t)h->blocks_per_sm_slim) {
+        // Fewer tiles than two waves of the persistent grid: the last wave
+        // would leave most CTA slots idle.  Halve the tile height where a
+        // 32-row k-split counterpart exists (64x8 -> 32x8, 64x32 -> 32x32),
+        // doubling those entries' tiles.
+        bool changed = false;
+        for (int& v : var) {
+            if (v == 0 || v == 2) {
+                v = v == 0 ? 6 : 7;
+                changed = true;
+            }
+        }
+        if (changed) make_tiles(host_descs, count, var, items);
+    }
     if (items.size() > 0x7fffffffull) {
         free_plan(p);
         return fail(LRB_ERR_INVALID, "too many tiles");
