@@ -68,6 +68,13 @@ struct Cfg {
     static constexpr int planeB = kTN * kc * 2;
     static constexpr int sbo = kc / 8 * 128;
     static constexpr int smem = 2 * S * (planeA + planeB);   // two stages
+    static constexpr int unitB = S * planeB + 256;           // pre-sliced B chunk: planes + 64 exponents
+};
+
+// One pre-sliced B chunk: columns [col0, col0 + 64) and rows [k0, k0 + kc)
+// of entry `entry`'s B.
+struct BUnit {
+    int32_t entry, col0, k0, pad;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -185,6 +192,69 @@ __device__ __forceinline__ double scaled_int_to_double(long long I, int X) {
     return __longlong_as_double((long long)b);
 }
 
+// The B part of one chunk, by 512 threads (warp w: columns 4w .. 4w + 3; lane:
+// k values lane + 32 h): column exponents F (to F_out[64]) and the S digit
+// planes (to planes, in the core-matrix layout the MMA reads).  Used by the
+// pre-pass, which writes to global memory; both use the same digit functions
+// as the in-kernel slicing, so the digits are the same whichever runs.
+template <bool FP16, int S>
+__device__ __forceinline__ void slice_b_chunk(const DevDesc& d, int n0, int k0, int warp, int lane,
+                                              uint8_t* planes, int* F_out) {
+    using C_ = Cfg<FP16, S>;
+    constexpr int BETA = C_::beta, KC = C_::kc, KB = KC / 32;
+    const int kcl = min(KC, d.k - k0);
+    const int wc = min(kTN, d.n - n0);
+#pragma unroll
+    for (int jc = 0; jc < 4; ++jc) {
+        const int j = 4 * warp + jc;
+        double bv[KB];
+        unsigned long long mx = 0;
+#pragma unroll
+        for (int h = 0; h < KB; ++h) {
+            const int kk = lane + 32 * h;
+            bv[h] = (j < wc && kk < kcl) ? __ldg(d.B + (size_t)(k0 + kk) + (size_t)(n0 + j) * (size_t)d.ldb) : 0.0;
+            const unsigned long long v = (unsigned long long)__double_as_longlong(bv[h]) & 0x7FFFFFFFFFFFFFFFull;
+            mx = v > mx ? v : mx;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long w = __shfl_xor_sync(0xffffffffu, mx, o);
+            mx = w > mx ? w : mx;
+        }
+        const int F = mx ? exp_of_bits(mx) : 0;
+        if (lane == 0) F_out[j] = F;
+        uint8_t* dst = planes + (j >> 3) * C_::sbo + (j & 7) * 16;
+#pragma unroll
+        for (int h = 0; h < KB; ++h) {
+            const int kk = lane + 32 * h;
+            int dg[S];
+            make_digits<S, BETA>(bv[h], F, dg);
+#pragma unroll
+            for (int s2 = 0; s2 < S; ++s2)
+                *reinterpret_cast<uint16_t*>(dst + s2 * C_::planeB + (kk >> 3) * 128 + (kk & 7) * 2) =
+                    digit_bits<FP16>(dg[s2]);
+        }
+    }
+}
+
+// Pre-pass: one 512-thread CTA per B unit (entry, 64-column tile, k-chunk).
+// Every 128-row tile of an entry uses the same B chunks; slicing them once
+// here instead of once per row tile removes the repeated integer work.
+template <bool FP16, int S>
+__global__ void __launch_bounds__(kThreadsS) k_slice_b(const DevDesc* __restrict__ descs,
+                                                       const BUnit* __restrict__ units, uint8_t* __restrict__ out) {
+    using C_ = Cfg<FP16, S>;
+    const BUnit u = units[blockIdx.x];
+    const DevDesc d = descs[u.entry];
+    uint8_t* dst = out + (size_t)blockIdx.x * C_::unitB;
+    slice_b_chunk<FP16, S>(d, u.col0, u.k0, threadIdx.x >> 5, threadIdx.x & 31, dst,
+                           reinterpret_cast<int*>(dst + S * C_::planeB));
+}
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem_dst)), "l"(src) : "memory");
+}
+
 // One CTA per SM, 512 threads, tiles taken round-robin (tile = 128 x 64
 // outputs).  The k-chunks of all of a CTA's tiles form one pipeline: while
 // the tensor cores run chunk i (digit planes and TMEM accumulator set i&1),
@@ -196,7 +266,10 @@ template <bool FP16, int S>
 __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restrict__ descs,
                                                          const SItem* __restrict__ items, int n_items,
                                                          int* __restrict__ status, float* __restrict__ dump,
-                                                         int test_stall) {
+                                                         int test_stall, const uint8_t* __restrict__ bunits,
+                                                         const long long* __restrict__ bfirst) {
+    // bunits != nullptr: B comes pre-sliced (k_slice_b), unit of (entry,
+    // column tile ct, chunk c) = bfirst[entry] + ct * chunks + c
     using C_ = Cfg<FP16, S>;
     constexpr int BETA = C_::beta, KC = C_::kc;
     constexpr int QC = KC / 4;            // chunk columns of A per thread
@@ -204,7 +277,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ unsigned long long s_rmax[4][kTM];
     __shared__ int s_E[2][kTM];
-    __shared__ int s_F[2][kTN];
+    __shared__ __align__(16) int s_F[2][kTN];
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ __align__(8) uint64_t s_never;   // test_stall: a barrier nothing arrives on
     __shared__ uint32_t s_tmem;
@@ -324,6 +397,14 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
             const int kcl = min(KC, d.k - k0);
             uint8_t* planeA = smem + stage * (S * (C_::planeA + C_::planeB));
             uint8_t* planeB = planeA + S * C_::planeA;
+            const bool pre = bunits != nullptr;
+            if (pre) {
+                // (0) this chunk's pre-sliced B: planes and exponents, 16 bytes per copy
+                const uint8_t* src = bunits + (size_t)(bfirst[item.entry] + (long long)(n0 / kTN) * nch + c) * C_::unitB;
+                for (int o = 16 * tid; o < S * C_::planeB; o += 16 * kThreadsS) cp_async16(planeB + o, src + o);
+                if (tid < kTN / 4) cp_async16(&s_F[stage][4 * tid], src + S * C_::planeB + 16 * tid);
+                asm volatile("cp.async.commit_group;\n" ::: "memory");
+            }
             // (1) loads: A row `row`, chunk columns [q QC, q QC + QC); B columns 4 w .. 4 w + 3
             double av[QC];
             {
@@ -336,14 +417,31 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
                 }
             }
             double bv[4][KB];
+            if (!pre) {
 #pragma unroll
-            for (int jc = 0; jc < 4; ++jc) {
-                const int j = 4 * warp + jc;
+                for (int jc = 0; jc < 4; ++jc) {
+                    const int j = 4 * warp + jc;
 #pragma unroll
-                for (int h = 0; h < KB; ++h) {
-                    const int kk = lane + 32 * h;
-                    bv[jc][h] = (j < wc && kk < kcl) ? __ldg(d.B + (size_t)(k0 + kk) + (size_t)(n0 + j) * (size_t)d.ldb)
-                                                     : 0.0;
+                    for (int h = 0; h < KB; ++h) {
+                        const int kk = lane + 32 * h;
+                        bv[jc][h] = (j < wc && kk < kcl)
+                                        ? __ldg(d.B + (size_t)(k0 + kk) + (size_t)(n0 + j) * (size_t)d.ldb)
+                                        : 0.0;
+                    }
+                }
+            }
+            // (1b) the tile's next chunk into L2 while this one is sliced and the
+            // previous one recombined: one 128-byte line per thread (A: 16 rows
+            // of one column; B: 16 k of one column), in-bounds addresses only
+            if (c + 1 < nch) {
+                const int kn = k0 + KC;
+                const int kk = tid >> 3, r = m0 + 16 * (tid & 7);
+                if (kk < KC && kn + kk < d.k && r < d.m)
+                    asm volatile("prefetch.global.L2 [%0];\n" ::"l"(d.A + (size_t)r + (size_t)(kn + kk) * (size_t)d.lda));
+                if (!pre && tid < kTN * (KC / 16)) {
+                    const int j = tid / (KC / 16), kb = kn + 16 * (tid % (KC / 16));
+                    if (j < wc && kb < d.k)
+                        asm volatile("prefetch.global.L2 [%0];\n" ::"l"(d.B + (size_t)kb + (size_t)(n0 + j) * (size_t)d.ldb));
                 }
             }
             // (2) exponents
@@ -356,21 +454,23 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
                 }
                 s_rmax[q][rloc] = mx;
             }
+            if (!pre) {
 #pragma unroll
-            for (int jc = 0; jc < 4; ++jc) {
-                unsigned long long mx = 0;
+                for (int jc = 0; jc < 4; ++jc) {
+                    unsigned long long mx = 0;
 #pragma unroll
-                for (int h = 0; h < KB; ++h) {
-                    const unsigned long long v =
-                        (unsigned long long)__double_as_longlong(bv[jc][h]) & 0x7FFFFFFFFFFFFFFFull;
-                    mx = v > mx ? v : mx;
+                    for (int h = 0; h < KB; ++h) {
+                        const unsigned long long v =
+                            (unsigned long long)__double_as_longlong(bv[jc][h]) & 0x7FFFFFFFFFFFFFFFull;
+                        mx = v > mx ? v : mx;
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const unsigned long long w = __shfl_xor_sync(0xffffffffu, mx, o);
+                        mx = w > mx ? w : mx;
+                    }
+                    if (lane == 0) s_F[stage][4 * warp + jc] = mx ? exp_of_bits(mx) : 0;
                 }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const unsigned long long w = __shfl_xor_sync(0xffffffffu, mx, o);
-                    mx = w > mx ? w : mx;
-                }
-                if (lane == 0) s_F[stage][4 * warp + jc] = mx ? exp_of_bits(mx) : 0;
             }
             __syncthreads();
             int E;
@@ -404,20 +504,24 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
                             make_uint4(packed[s2][0], packed[s2][1], packed[s2][2], packed[s2][3]);
                 }
             }
+            if (pre) {
+                asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+            } else {
 #pragma unroll
-            for (int jc = 0; jc < 4; ++jc) {
-                const int j = 4 * warp + jc;
-                const int F = s_F[stage][j];
-                uint8_t* dst = planeB + (j >> 3) * C_::sbo + (j & 7) * 16;
+                for (int jc = 0; jc < 4; ++jc) {
+                    const int j = 4 * warp + jc;
+                    const int F = s_F[stage][j];
+                    uint8_t* dst = planeB + (j >> 3) * C_::sbo + (j & 7) * 16;
 #pragma unroll
-                for (int h = 0; h < KB; ++h) {
-                    const int kk = lane + 32 * h;
-                    int dg[S];
-                    make_digits<S, BETA>(bv[jc][h], F, dg);
+                    for (int h = 0; h < KB; ++h) {
+                        const int kk = lane + 32 * h;
+                        int dg[S];
+                        make_digits<S, BETA>(bv[jc][h], F, dg);
 #pragma unroll
-                    for (int s2 = 0; s2 < S; ++s2)
-                        *reinterpret_cast<uint16_t*>(dst + s2 * C_::planeB + (kk >> 3) * 128 + (kk & 7) * 2) =
-                            digit_bits<FP16>(dg[s2]);
+                        for (int s2 = 0; s2 < S; ++s2)
+                            *reinterpret_cast<uint16_t*>(dst + s2 * C_::planeB + (kk >> 3) * 128 + (kk & 7) * 2) =
+                                digit_bits<FP16>(dg[s2]);
+                    }
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -497,7 +601,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
 
 template <bool FP16, int S>
 cudaError_t launch_t(const DevDesc* descs, const SItem* items, int n_items, int* status, float* dump,
-                     int test_stall, cudaStream_t s) {
+                     int test_stall, const uint8_t* bunits, const long long* bfirst, cudaStream_t s) {
     const int smem = Cfg<FP16, S>::smem;
     cudaError_t e = cudaFuncSetAttribute(k_split<FP16, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
@@ -506,17 +610,49 @@ cudaError_t launch_t(const DevDesc* descs, const SItem* items, int n_items, int*
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = std::max(1, std::min(n_items, sms));
-    k_split<FP16, S><<<grid, kThreadsS, smem, s>>>(descs, items, n_items, status, dump, test_stall);
+    k_split<FP16, S><<<grid, kThreadsS, smem, s>>>(descs, items, n_items, status, dump, test_stall, bunits, bfirst);
     return cudaGetLastError();
 }
 
-cudaError_t launch_prec(int precision, const DevDesc* descs, const SItem* items, int n_items, int* status,
-                        float* dump, int test_stall, cudaStream_t s) {
+template <bool FP16, int S>
+cudaError_t slice_t(const DevDesc* descs, const BUnit* units, int n_units, uint8_t* out, cudaStream_t s) {
+    if (n_units <= 0) return cudaSuccess;
+    k_slice_b<FP16, S><<<n_units, kThreadsS, 0, s>>>(descs, units, out);
+    return cudaGetLastError();
+}
+
+cudaError_t slice_prec(int precision, const DevDesc* descs, const BUnit* units, int n_units, uint8_t* out,
+                       cudaStream_t s) {
     switch (precision) {
-        case LRB_PREC_SPLIT_BF16_S3: return launch_t<false, 3>(descs, items, n_items, status, dump, test_stall, s);
-        case LRB_PREC_SPLIT_BF16_S4: return launch_t<false, 4>(descs, items, n_items, status, dump, test_stall, s);
-        case LRB_PREC_SPLIT_FP16_S3: return launch_t<true, 3>(descs, items, n_items, status, dump, test_stall, s);
-        case LRB_PREC_SPLIT_FP16_S4: return launch_t<true, 4>(descs, items, n_items, status, dump, test_stall, s);
+        case LRB_PREC_SPLIT_BF16_S3: return slice_t<false, 3>(descs, units, n_units, out, s);
+        case LRB_PREC_SPLIT_BF16_S4: return slice_t<false, 4>(descs, units, n_units, out, s);
+        case LRB_PREC_SPLIT_FP16_S3: return slice_t<true, 3>(descs, units, n_units, out, s);
+        case LRB_PREC_SPLIT_FP16_S4: return slice_t<true, 4>(descs, units, n_units, out, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+size_t unit_bytes(int precision) {
+    switch (precision) {
+        case LRB_PREC_SPLIT_BF16_S3: return Cfg<false, 3>::unitB;
+        case LRB_PREC_SPLIT_BF16_S4: return Cfg<false, 4>::unitB;
+        case LRB_PREC_SPLIT_FP16_S3: return Cfg<true, 3>::unitB;
+        default: return Cfg<true, 4>::unitB;
+    }
+}
+
+cudaError_t launch_prec(int precision, const DevDesc* descs, const SItem* items, int n_items, int* status,
+                        float* dump, int test_stall, const uint8_t* bunits, const long long* bfirst,
+                        cudaStream_t s) {
+    switch (precision) {
+        case LRB_PREC_SPLIT_BF16_S3:
+            return launch_t<false, 3>(descs, items, n_items, status, dump, test_stall, bunits, bfirst, s);
+        case LRB_PREC_SPLIT_BF16_S4:
+            return launch_t<false, 4>(descs, items, n_items, status, dump, test_stall, bunits, bfirst, s);
+        case LRB_PREC_SPLIT_FP16_S3:
+            return launch_t<true, 3>(descs, items, n_items, status, dump, test_stall, bunits, bfirst, s);
+        case LRB_PREC_SPLIT_FP16_S4:
+            return launch_t<true, 4>(descs, items, n_items, status, dump, test_stall, bunits, bfirst, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -531,6 +667,11 @@ struct SplitPlan {
     SItem* d_items = nullptr;
     int* d_status = nullptr;
     int n_items = 0;
+    // pre-sliced B (nullptr: the kernel slices B itself)
+    uint8_t* bunits = nullptr;
+    BUnit* d_units = nullptr;
+    long long* d_bfirst = nullptr;
+    int n_units = 0;
 };
 
 void build_items(const lrb_gemm_desc* descs, size_t count, std::vector<int4>& items) {
@@ -543,7 +684,8 @@ void build_items(const lrb_gemm_desc* descs, size_t count, std::vector<int4>& it
 cudaError_t launch_raw(int precision, const DevDesc* d_descs, const int4* d_items, int n_items, int* d_status,
                        cudaStream_t s) {
     static_assert(sizeof(int4) == sizeof(SItem), "tile layout");
-    return launch_prec(precision, d_descs, reinterpret_cast<const SItem*>(d_items), n_items, d_status, nullptr, 0, s);
+    return launch_prec(precision, d_descs, reinterpret_cast<const SItem*>(d_items), n_items, d_status, nullptr, 0,
+                       nullptr, nullptr, s);
 }
 
 int chunk_len(int precision) {
@@ -591,6 +733,40 @@ lrb_status create(int device, int sms, const lrb_gemm_desc* descs, size_t count,
         set_last_error("split plan upload");
         return LRB_ERR_DEVICE;
     }
+    // B units: every (entry, 64-column tile, k-chunk), entries in order; sliced
+    // by a pre-pass when they fit in memory (else the kernel slices B itself)
+    {
+        const int kc = chunk_len(precision);
+        std::vector<BUnit> units;
+        std::vector<long long> first(count);
+        for (size_t e = 0; e < count; ++e) {
+            first[e] = (long long)units.size();
+            for (int c0 = 0; c0 < descs[e].n; c0 += kTN)
+                for (int k0 = 0; k0 < descs[e].k; k0 += kc) units.push_back(BUnit{(int32_t)e, c0, k0, 0});
+        }
+        const size_t ub = unit_bytes(precision);
+        void* mem = nullptr;
+        if (units.size() < 0x7fffffffull &&
+            cudaMalloc(&mem, ub * units.size() + sizeof(BUnit) * units.size() + sizeof(long long) * count + 512) ==
+                cudaSuccess) {
+            p->bunits = (uint8_t*)mem;
+            p->d_units = (BUnit*)(p->bunits + ((ub * units.size() + 255) / 256) * 256);
+            p->d_bfirst = (long long*)((char*)p->d_units + ((sizeof(BUnit) * units.size() + 255) / 256) * 256);
+            p->n_units = (int)units.size();
+            ce = cudaMemcpy(p->d_units, units.data(), sizeof(BUnit) * units.size(), cudaMemcpyHostToDevice);
+            if (ce == cudaSuccess)
+                ce = cudaMemcpy(p->d_bfirst, first.data(), sizeof(long long) * count, cudaMemcpyHostToDevice);
+            if (ce != cudaSuccess) {
+                cudaFree(mem);
+                cudaFree(p->dmem);
+                delete p;
+                set_last_error("split plan upload");
+                return LRB_ERR_DEVICE;
+            }
+        } else {
+            cudaGetLastError();   // a failed allocation leaves the in-kernel slicing
+        }
+    }
     info->items = p->n_items;
     info->groups = 1;
     int dev = 0, nsm = 0;
@@ -602,11 +778,21 @@ lrb_status create(int device, int sms, const lrb_gemm_desc* descs, size_t count,
 }
 
 cudaError_t launch(SplitPlan* p, cudaStream_t s) {
-    return launch_prec(p->precision, p->d_descs, p->d_items, p->n_items, p->d_status, nullptr, p->test_stall, s);
+    if (p->bunits) {
+        cudaError_t e = slice_prec(p->precision, p->d_descs, p->d_units, p->n_units, p->bunits, s);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_prec(p->precision, p->d_descs, p->d_items, p->n_items, p->d_status, nullptr, p->test_stall,
+                       p->bunits, p->d_bfirst, s);
 }
 
 cudaError_t launch_dump(SplitPlan* p, float* dump, cudaStream_t s) {
-    return launch_prec(p->precision, p->d_descs, p->d_items, p->n_items, p->d_status, dump, p->test_stall, s);
+    if (p->bunits) {
+        cudaError_t e = slice_prec(p->precision, p->d_descs, p->d_units, p->n_units, p->bunits, s);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_prec(p->precision, p->d_descs, p->d_items, p->n_items, p->d_status, dump, p->test_stall,
+                       p->bunits, p->d_bfirst, s);
 }
 
 int read_status(SplitPlan* p, cudaStream_t s, int* value) {
@@ -617,6 +803,7 @@ int read_status(SplitPlan* p, cudaStream_t s, int* value) {
 
 void destroy(SplitPlan* p) {
     if (!p) return;
+    if (p->bunits) cudaFree(p->bunits);
     if (p->dmem) cudaFree(p->dmem);
     delete p;
 }
