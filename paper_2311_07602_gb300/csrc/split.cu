@@ -69,10 +69,12 @@ struct Cfg {
     static constexpr int sbo = kc / 8 * 128;
     static constexpr int smem = 2 * S * (planeA + planeB);   // two stages
     static constexpr int unitB = S * planeB + 256;           // pre-sliced B chunk: planes + 64 exponents
+    static constexpr int unitA = S * planeA + 512;           // pre-sliced A chunk: planes + 128 exponents
 };
 
 // One pre-sliced B chunk: columns [col0, col0 + 64) and rows [k0, k0 + kc)
-// of entry `entry`'s B.
+// of entry `entry`'s B.  An A unit is rows [row0, row0 + 128) and columns
+// [k0, k0 + kc) of A (the same struct, col0 read as row0).
 struct BUnit {
     int32_t entry, col0, k0, pad;
 };
@@ -251,6 +253,67 @@ __global__ void __launch_bounds__(kThreadsS) k_slice_b(const DevDesc* __restrict
                            reinterpret_cast<int*>(dst + S * C_::planeB));
 }
 
+// Pre-pass for entries with several 64-column tiles (each 128-row tile of A
+// would otherwise be sliced once per column tile): one 512-thread CTA per A
+// unit; thread (row 32 (w % 4) + lane, quarter w / 4 of the chunk) as in the
+// main kernel, row exponents through shared memory, digit planes and the 128
+// exponents written to global memory.
+template <bool FP16, int S>
+__global__ void __launch_bounds__(kThreadsS) k_slice_a(const DevDesc* __restrict__ descs,
+                                                       const BUnit* __restrict__ units, uint8_t* __restrict__ out) {
+    using C_ = Cfg<FP16, S>;
+    constexpr int BETA = C_::beta, KC = C_::kc, QC = KC / 4;
+    __shared__ unsigned long long s_rmax[4][kTM];
+    const BUnit u = units[blockIdx.x];
+    const DevDesc d = descs[u.entry];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rloc = 32 * (warp & 3) + lane, q = warp >> 2;
+    const int row = u.col0 + rloc, k0 = u.k0;
+    const int kcl = min(KC, d.k - k0);
+    uint8_t* dst0 = out + (size_t)blockIdx.x * C_::unitA;
+    double av[QC];
+    {
+        const double* ap = d.A + (size_t)row + (size_t)(k0 + q * QC) * (size_t)d.lda;
+        const int ncol = row < d.m ? min(QC, kcl - q * QC) : 0;
+#pragma unroll
+        for (int p = 0; p < QC; ++p) {
+            av[p] = p < ncol ? __ldg(ap) : 0.0;
+            ap += d.lda;
+        }
+    }
+    unsigned long long mx = 0;
+#pragma unroll
+    for (int p = 0; p < QC; ++p) {
+        const unsigned long long v = (unsigned long long)__double_as_longlong(av[p]) & 0x7FFFFFFFFFFFFFFFull;
+        mx = v > mx ? v : mx;
+    }
+    s_rmax[q][rloc] = mx;
+    __syncthreads();
+    mx = s_rmax[0][rloc];
+#pragma unroll
+    for (int qq = 1; qq < 4; ++qq) mx = s_rmax[qq][rloc] > mx ? s_rmax[qq][rloc] : mx;
+    const int E = mx ? exp_of_bits(mx) : 0;
+    if (q == 0) reinterpret_cast<int*>(dst0 + S * C_::planeA)[rloc] = E;
+    uint8_t* dst = dst0 + (rloc >> 3) * C_::sbo + (rloc & 7) * 16 + (q * QC / 8) * 128;
+#pragma unroll
+    for (int g = 0; g < QC / 8; ++g) {
+        uint32_t packed[S][4];
+#pragma unroll
+        for (int p = 0; p < 8; p += 2) {
+            int d0[S], d1[S];
+            make_digits<S, BETA>(av[8 * g + p], E, d0);
+            make_digits<S, BETA>(av[8 * g + p + 1], E, d1);
+#pragma unroll
+            for (int s2 = 0; s2 < S; ++s2)
+                packed[s2][p >> 1] = (uint32_t)digit_bits<FP16>(d0[s2]) | ((uint32_t)digit_bits<FP16>(d1[s2]) << 16);
+        }
+#pragma unroll
+        for (int s2 = 0; s2 < S; ++s2)
+            *reinterpret_cast<uint4*>(dst + s2 * C_::planeA + g * 128) =
+                make_uint4(packed[s2][0], packed[s2][1], packed[s2][2], packed[s2][3]);
+    }
+}
+
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem_dst)), "l"(src) : "memory");
 }
@@ -262,21 +325,26 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* src) {
 // slice chunk i+1.  Thread t: row 32 (w % 4) + lane of the tile (w = warp,
 // = its TMEM lane), quarter q = w / 4 of the chunk's columns for slicing and
 // of the tile's 64 output columns for recombination.
-template <bool FP16, int S>
+template <bool FP16, int S, int MODE>
 __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restrict__ descs,
                                                          const SItem* __restrict__ items, int n_items,
                                                          int* __restrict__ status, float* __restrict__ dump,
                                                          int test_stall, const uint8_t* __restrict__ bunits,
-                                                         const long long* __restrict__ bfirst) {
-    // bunits != nullptr: B comes pre-sliced (k_slice_b), unit of (entry,
-    // column tile ct, chunk c) = bfirst[entry] + ct * chunks + c
+                                                         const long long* __restrict__ bfirst,
+                                                         const uint8_t* __restrict__ aunits,
+                                                         const long long* __restrict__ afirst) {
+    // MODE 0: the kernel slices A and B (serving waves).  MODE 1: B comes
+    // pre-sliced (k_slice_b), unit of (entry, column tile ct, chunk c) =
+    // bfirst[entry] + ct * chunks + c.  MODE 2: A too (k_slice_a), unit
+    // afirst[entry] + row tile * chunks + c (entries with several column tiles).
+    constexpr bool PRE = MODE >= 1;
     using C_ = Cfg<FP16, S>;
     constexpr int BETA = C_::beta, KC = C_::kc;
     constexpr int QC = KC / 4;            // chunk columns of A per thread
     constexpr int KB = KC / 32;           // k values of B per lane and column
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ unsigned long long s_rmax[4][kTM];
-    __shared__ int s_E[2][kTM];
+    __shared__ __align__(16) int s_E[2][kTM];
     __shared__ __align__(16) int s_F[2][kTN];
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ __align__(8) uint64_t s_never;   // test_stall: a barrier nothing arrives on
@@ -306,7 +374,8 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
 
     // the chunk whose MMAs are in flight (recombined one iteration later)
     struct Prev {
-        DevDesc d;
+        double* C;          // the tile's entry: C, its extent and leading dimension
+        int m, n, ldc;
         int row0, col0, c, stage;
         bool last;
     } prev{};
@@ -350,10 +419,10 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
 #pragma unroll
                 for (int l = 0; l < S; ++l)   // level L = l + 2, weight 2^(beta (S - 1 - l))
                     I = I * (1ll << BETA) + (long long)__float2int_rn(__uint_as_float(v[l][jj]));
-                if (dump != nullptr && row < prev.d.m && prev.col0 + j < prev.d.n) {
+                if (dump != nullptr && row < prev.m && prev.col0 + j < prev.n) {
 #pragma unroll
                     for (int l = 0; l < S; ++l)
-                        dump[(((size_t)prev.c * S + l) * prev.d.m + row) * prev.d.n + (prev.col0 + j)] =
+                        dump[(((size_t)prev.c * S + l) * prev.m + row) * prev.n + (prev.col0 + j)] =
                             __uint_as_float(v[l][jj]);
                 }
                 // the exact binary64 value I 2^X (built from bits with integer
@@ -367,11 +436,11 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
 
     auto store_prev = [&]() {
         const int row = prev.row0 + rloc;
-        if (row < prev.d.m) {
+        if (row < prev.m) {
 #pragma unroll
             for (int jj = 0; jj < 16; ++jj) {
                 const int col = prev.col0 + 16 * q + jj;
-                if (col < prev.d.n) prev.d.C[(size_t)row + (size_t)col * (size_t)prev.d.ldc] = acc[jj];
+                if (col < prev.n) prev.C[(size_t)row + (size_t)col * (size_t)prev.ldc] = acc[jj];
             }
         }
     };
@@ -397,8 +466,15 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
             const int kcl = min(KC, d.k - k0);
             uint8_t* planeA = smem + stage * (S * (C_::planeA + C_::planeB));
             uint8_t* planeB = planeA + S * C_::planeA;
-            const bool pre = bunits != nullptr;
-            if (pre) {
+            constexpr bool pre = PRE;
+            constexpr bool preA = MODE == 2;
+            if constexpr (preA) {
+                const uint8_t* src = aunits + (size_t)(afirst[item.entry] + (long long)(m0 / kTM) * nch + c) * C_::unitA;
+                for (int o = 16 * tid; o < S * C_::planeA; o += 16 * kThreadsS) cp_async16(planeA + o, src + o);
+                if (tid < kTM / 4) cp_async16(&s_E[stage][4 * tid], src + S * C_::planeA + 16 * tid);
+                asm volatile("cp.async.commit_group;\n" ::: "memory");
+            }
+            if constexpr (PRE) {
                 // (0) this chunk's pre-sliced B: planes and exponents, 16 bytes per copy
                 const uint8_t* src = bunits + (size_t)(bfirst[item.entry] + (long long)(n0 / kTN) * nch + c) * C_::unitB;
                 for (int o = 16 * tid; o < S * C_::planeB; o += 16 * kThreadsS) cp_async16(planeB + o, src + o);
@@ -406,8 +482,8 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
                 asm volatile("cp.async.commit_group;\n" ::: "memory");
             }
             // (1) loads: A row `row`, chunk columns [q QC, q QC + QC); B columns 4 w .. 4 w + 3
-            double av[QC];
-            {
+            double av[preA ? 1 : QC];
+            if constexpr (!preA) {
                 const double* ap = d.A + (size_t)row + (size_t)(k0 + q * QC) * (size_t)d.lda;
                 const int ncol = row_ok ? min(QC, kcl - q * QC) : 0;   // valid columns of this quarter
 #pragma unroll
@@ -416,8 +492,8 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
                     ap += d.lda;
                 }
             }
-            double bv[4][KB];
-            if (!pre) {
+            double bv[PRE ? 1 : 4][KB];
+            if constexpr (!PRE) {
 #pragma unroll
                 for (int jc = 0; jc < 4; ++jc) {
                     const int j = 4 * warp + jc;
@@ -436,16 +512,16 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
             if (c + 1 < nch) {
                 const int kn = k0 + KC;
                 const int kk = tid >> 3, r = m0 + 16 * (tid & 7);
-                if (kk < KC && kn + kk < d.k && r < d.m)
+                if (!preA && kk < KC && kn + kk < d.k && r < d.m)
                     asm volatile("prefetch.global.L2 [%0];\n" ::"l"(d.A + (size_t)r + (size_t)(kn + kk) * (size_t)d.lda));
-                if (!pre && tid < kTN * (KC / 16)) {
+                if (!PRE && tid < kTN * (KC / 16)) {
                     const int j = tid / (KC / 16), kb = kn + 16 * (tid % (KC / 16));
                     if (j < wc && kb < d.k)
                         asm volatile("prefetch.global.L2 [%0];\n" ::"l"(d.B + (size_t)kb + (size_t)(n0 + j) * (size_t)d.ldb));
                 }
             }
             // (2) exponents
-            {
+            if constexpr (!preA) {
                 unsigned long long mx = 0;
 #pragma unroll
                 for (int p = 0; p < QC; ++p) {
@@ -454,7 +530,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
                 }
                 s_rmax[q][rloc] = mx;
             }
-            if (!pre) {
+            if constexpr (!PRE) {
 #pragma unroll
                 for (int jc = 0; jc < 4; ++jc) {
                     unsigned long long mx = 0;
@@ -472,9 +548,9 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
                     if (lane == 0) s_F[stage][4 * warp + jc] = mx ? exp_of_bits(mx) : 0;
                 }
             }
-            __syncthreads();
-            int E;
-            {
+            if (!(preA && pre)) __syncthreads();   // row / column exponents exchanged
+            int E = 0;
+            if constexpr (!preA) {
                 unsigned long long mx = s_rmax[0][rloc];
 #pragma unroll
                 for (int qq = 1; qq < 4; ++qq) mx = s_rmax[qq][rloc] > mx ? s_rmax[qq][rloc] : mx;
@@ -483,7 +559,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
             }
             // (3) digits into the planes of this stage (free: their MMAs were
             // waited for when the previous chunk was recombined)
-            {
+            if constexpr (!preA) {
                 uint8_t* dst = planeA + (rloc >> 3) * C_::sbo + (rloc & 7) * 16 + (q * QC / 8) * 128;
 #pragma unroll
                 for (int g = 0; g < QC / 8; ++g) {
@@ -504,9 +580,8 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
                             make_uint4(packed[s2][0], packed[s2][1], packed[s2][2], packed[s2][3]);
                 }
             }
-            if (pre) {
-                asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-            } else {
+            if (PRE) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+            if constexpr (!PRE) {
 #pragma unroll
                 for (int jc = 0; jc < 4; ++jc) {
                     const int j = 4 * warp + jc;
@@ -571,7 +646,10 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
                     load_c0(d, m0, n0);   // chunk c is chunk 0 of this tile; consumed next iteration
                 }
             }
-            prev.d = d;
+            prev.C = d.C;
+            prev.m = d.m;
+            prev.n = d.n;
+            prev.ldc = d.ldc;
             prev.row0 = m0;
             prev.col0 = n0;
             prev.c = c;
@@ -599,60 +677,87 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
 }
 
-template <bool FP16, int S>
-cudaError_t launch_t(const DevDesc* descs, const SItem* items, int n_items, int* status, float* dump,
-                     int test_stall, const uint8_t* bunits, const long long* bfirst, cudaStream_t s) {
+template <bool FP16, int S, int MODE>
+cudaError_t launch_mode(const DevDesc* descs, const SItem* items, int n_items, int* status, float* dump,
+                        int test_stall, const uint8_t* bunits, const long long* bfirst, const uint8_t* aunits,
+                        const long long* afirst, cudaStream_t s) {
     const int smem = Cfg<FP16, S>::smem;
-    cudaError_t e = cudaFuncSetAttribute(k_split<FP16, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(k_split<FP16, S, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     if (n_items <= 0) return cudaSuccess;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = std::max(1, std::min(n_items, sms));
-    k_split<FP16, S><<<grid, kThreadsS, smem, s>>>(descs, items, n_items, status, dump, test_stall, bunits, bfirst);
+    k_split<FP16, S, MODE><<<grid, kThreadsS, smem, s>>>(descs, items, n_items, status, dump, test_stall, bunits,
+                                                         bfirst, aunits, afirst);
     return cudaGetLastError();
+}
+
+// Items [0, n_b) take mode 1 (or 0 without pre-sliced B), items [n_b, n_items)
+// mode 2 (their entries have pre-sliced A): two launches in stream order.
+template <bool FP16, int S>
+cudaError_t launch_t(const DevDesc* descs, const SItem* items, int n_items, int n_b, int* status, float* dump,
+                     int test_stall, const uint8_t* bunits, const long long* bfirst, const uint8_t* aunits,
+                     const long long* afirst, cudaStream_t s) {
+    if (bunits == nullptr)
+        return launch_mode<FP16, S, 0>(descs, items, n_items, status, dump, test_stall, nullptr, nullptr, nullptr,
+                                       nullptr, s);
+    cudaError_t e = launch_mode<FP16, S, 1>(descs, items, n_b, status, dump, test_stall, bunits, bfirst, nullptr,
+                                            nullptr, s);
+    if (e == cudaSuccess && n_items > n_b)
+        e = launch_mode<FP16, S, 2>(descs, items + n_b, n_items - n_b, status, dump, test_stall, bunits, bfirst,
+                                    aunits, afirst, s);
+    return e;
 }
 
 template <bool FP16, int S>
-cudaError_t slice_t(const DevDesc* descs, const BUnit* units, int n_units, uint8_t* out, cudaStream_t s) {
+cudaError_t slice_t(bool a_side, const DevDesc* descs, const BUnit* units, int n_units, uint8_t* out,
+                    cudaStream_t s) {
     if (n_units <= 0) return cudaSuccess;
-    k_slice_b<FP16, S><<<n_units, kThreadsS, 0, s>>>(descs, units, out);
+    if (a_side)
+        k_slice_a<FP16, S><<<n_units, kThreadsS, 0, s>>>(descs, units, out);
+    else
+        k_slice_b<FP16, S><<<n_units, kThreadsS, 0, s>>>(descs, units, out);
     return cudaGetLastError();
 }
 
-cudaError_t slice_prec(int precision, const DevDesc* descs, const BUnit* units, int n_units, uint8_t* out,
-                       cudaStream_t s) {
+cudaError_t slice_prec(int precision, bool a_side, const DevDesc* descs, const BUnit* units, int n_units,
+                       uint8_t* out, cudaStream_t s) {
     switch (precision) {
-        case LRB_PREC_SPLIT_BF16_S3: return slice_t<false, 3>(descs, units, n_units, out, s);
-        case LRB_PREC_SPLIT_BF16_S4: return slice_t<false, 4>(descs, units, n_units, out, s);
-        case LRB_PREC_SPLIT_FP16_S3: return slice_t<true, 3>(descs, units, n_units, out, s);
-        case LRB_PREC_SPLIT_FP16_S4: return slice_t<true, 4>(descs, units, n_units, out, s);
+        case LRB_PREC_SPLIT_BF16_S3: return slice_t<false, 3>(a_side, descs, units, n_units, out, s);
+        case LRB_PREC_SPLIT_BF16_S4: return slice_t<false, 4>(a_side, descs, units, n_units, out, s);
+        case LRB_PREC_SPLIT_FP16_S3: return slice_t<true, 3>(a_side, descs, units, n_units, out, s);
+        case LRB_PREC_SPLIT_FP16_S4: return slice_t<true, 4>(a_side, descs, units, n_units, out, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
-size_t unit_bytes(int precision) {
+size_t unit_bytes(int precision, bool a_side) {
     switch (precision) {
-        case LRB_PREC_SPLIT_BF16_S3: return Cfg<false, 3>::unitB;
-        case LRB_PREC_SPLIT_BF16_S4: return Cfg<false, 4>::unitB;
-        case LRB_PREC_SPLIT_FP16_S3: return Cfg<true, 3>::unitB;
-        default: return Cfg<true, 4>::unitB;
+        case LRB_PREC_SPLIT_BF16_S3: return a_side ? Cfg<false, 3>::unitA : Cfg<false, 3>::unitB;
+        case LRB_PREC_SPLIT_BF16_S4: return a_side ? Cfg<false, 4>::unitA : Cfg<false, 4>::unitB;
+        case LRB_PREC_SPLIT_FP16_S3: return a_side ? Cfg<true, 3>::unitA : Cfg<true, 3>::unitB;
+        default: return a_side ? Cfg<true, 4>::unitA : Cfg<true, 4>::unitB;
     }
 }
 
-cudaError_t launch_prec(int precision, const DevDesc* descs, const SItem* items, int n_items, int* status,
+cudaError_t launch_prec(int precision, const DevDesc* descs, const SItem* items, int n_items, int n_b, int* status,
                         float* dump, int test_stall, const uint8_t* bunits, const long long* bfirst,
-                        cudaStream_t s) {
+                        const uint8_t* aunits, const long long* afirst, cudaStream_t s) {
     switch (precision) {
         case LRB_PREC_SPLIT_BF16_S3:
-            return launch_t<false, 3>(descs, items, n_items, status, dump, test_stall, bunits, bfirst, s);
+            return launch_t<false, 3>(descs, items, n_items, n_b, status, dump, test_stall, bunits, bfirst, aunits,
+                                      afirst, s);
         case LRB_PREC_SPLIT_BF16_S4:
-            return launch_t<false, 4>(descs, items, n_items, status, dump, test_stall, bunits, bfirst, s);
+            return launch_t<false, 4>(descs, items, n_items, n_b, status, dump, test_stall, bunits, bfirst, aunits,
+                                      afirst, s);
         case LRB_PREC_SPLIT_FP16_S3:
-            return launch_t<true, 3>(descs, items, n_items, status, dump, test_stall, bunits, bfirst, s);
+            return launch_t<true, 3>(descs, items, n_items, n_b, status, dump, test_stall, bunits, bfirst, aunits,
+                                     afirst, s);
         case LRB_PREC_SPLIT_FP16_S4:
-            return launch_t<true, 4>(descs, items, n_items, status, dump, test_stall, bunits, bfirst, s);
+            return launch_t<true, 4>(descs, items, n_items, n_b, status, dump, test_stall, bunits, bfirst, aunits,
+                                     afirst, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -667,11 +772,17 @@ struct SplitPlan {
     SItem* d_items = nullptr;
     int* d_status = nullptr;
     int n_items = 0;
-    // pre-sliced B (nullptr: the kernel slices B itself)
+    // pre-sliced B (nullptr: the kernel slices B itself) and A (entries with
+    // several column tiles only); one allocation, freed through bunits
     uint8_t* bunits = nullptr;
     BUnit* d_units = nullptr;
     long long* d_bfirst = nullptr;
     int n_units = 0;
+    uint8_t* aunits = nullptr;
+    BUnit* d_aunits = nullptr;
+    long long* d_afirst = nullptr;
+    int n_aunits = 0;
+    int n_items_b = 0;   // items [0, n_items_b) have A sliced in the kernel, the rest pre-sliced
 };
 
 void build_items(const lrb_gemm_desc* descs, size_t count, std::vector<int4>& items) {
@@ -684,8 +795,8 @@ void build_items(const lrb_gemm_desc* descs, size_t count, std::vector<int4>& it
 cudaError_t launch_raw(int precision, const DevDesc* d_descs, const int4* d_items, int n_items, int* d_status,
                        cudaStream_t s) {
     static_assert(sizeof(int4) == sizeof(SItem), "tile layout");
-    return launch_prec(precision, d_descs, reinterpret_cast<const SItem*>(d_items), n_items, d_status, nullptr, 0,
-                       nullptr, nullptr, s);
+    return launch_prec(precision, d_descs, reinterpret_cast<const SItem*>(d_items), n_items, n_items, d_status,
+                       nullptr, 0, nullptr, nullptr, nullptr, nullptr, s);
 }
 
 int chunk_len(int precision) {
@@ -700,10 +811,17 @@ lrb_status create(int device, int sms, const lrb_gemm_desc* descs, size_t count,
     (void)device;
     (void)sms;
     *out = nullptr;
+    // tiles of entries with one column tile first (their A is sliced in the
+    // kernel), then the entries whose A is pre-sliced (several column tiles)
     std::vector<SItem> items;
+    for (int pass = 0; pass < 2; ++pass)
+        for (size_t e = 0; e < count; ++e)
+            if ((descs[e].n > kTN) == (pass == 1))
+                for (int c0 = 0; c0 < descs[e].n; c0 += kTN)
+                    for (int r0 = 0; r0 < descs[e].m; r0 += kTM) items.push_back(SItem{(int32_t)e, r0, c0, 0});
+    size_t n_items_b = 0;
     for (size_t e = 0; e < count; ++e)
-        for (int c0 = 0; c0 < descs[e].n; c0 += kTN)
-            for (int r0 = 0; r0 < descs[e].m; r0 += kTM) items.push_back(SItem{(int32_t)e, r0, c0, 0});
+        if (descs[e].n <= kTN) n_items_b += (size_t)((descs[e].m + kTM - 1) / kTM);
     if (items.size() > 0x7fffffffull) {
         set_last_error("too many split-precision tiles");
         return LRB_ERR_INVALID;
@@ -723,6 +841,7 @@ lrb_status create(int device, int sms, const lrb_gemm_desc* descs, size_t count,
     p->d_items = (SItem*)((char*)p->dmem + o_items);
     p->d_status = (int*)((char*)p->dmem + o_status);
     p->n_items = (int)items.size();
+    p->n_items_b = (int)n_items_b;
     ce = cudaMemcpy(p->d_descs, descs, sizeof(DevDesc) * count, cudaMemcpyHostToDevice);
     if (ce == cudaSuccess && !items.empty())
         ce = cudaMemcpy(p->d_items, items.data(), sizeof(SItem) * items.size(), cudaMemcpyHostToDevice);
@@ -733,29 +852,48 @@ lrb_status create(int device, int sms, const lrb_gemm_desc* descs, size_t count,
         set_last_error("split plan upload");
         return LRB_ERR_DEVICE;
     }
-    // B units: every (entry, 64-column tile, k-chunk), entries in order; sliced
-    // by a pre-pass when they fit in memory (else the kernel slices B itself)
+    // B units: every (entry, 64-column tile, k-chunk); A units: every (entry,
+    // 128-row tile, k-chunk) of entries with more than one column tile.
+    // Sliced by pre-passes when they fit in memory (else the kernel slices).
     {
         const int kc = chunk_len(precision);
-        std::vector<BUnit> units;
-        std::vector<long long> first(count);
+        std::vector<BUnit> bu, au;
+        std::vector<long long> bfirst(count), afirst(count, -1);
         for (size_t e = 0; e < count; ++e) {
-            first[e] = (long long)units.size();
+            bfirst[e] = (long long)bu.size();
             for (int c0 = 0; c0 < descs[e].n; c0 += kTN)
-                for (int k0 = 0; k0 < descs[e].k; k0 += kc) units.push_back(BUnit{(int32_t)e, c0, k0, 0});
+                for (int k0 = 0; k0 < descs[e].k; k0 += kc) bu.push_back(BUnit{(int32_t)e, c0, k0, 0});
+            if (descs[e].n > kTN) {
+                afirst[e] = (long long)au.size();
+                for (int r0 = 0; r0 < descs[e].m; r0 += kTM)
+                    for (int k0 = 0; k0 < descs[e].k; k0 += kc) au.push_back(BUnit{(int32_t)e, r0, k0, 0});
+            }
         }
-        const size_t ub = unit_bytes(precision);
+        auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+        const size_t ubB = unit_bytes(precision, false), ubA = unit_bytes(precision, true);
+        const size_t oB = 0, oBu = oB + up(ubB * bu.size()), oBf = oBu + up(sizeof(BUnit) * bu.size());
+        const size_t oA = oBf + up(sizeof(long long) * count), oAu = oA + up(ubA * au.size());
+        const size_t oAf = oAu + up(sizeof(BUnit) * au.size()), total = oAf + up(sizeof(long long) * count);
         void* mem = nullptr;
-        if (units.size() < 0x7fffffffull &&
-            cudaMalloc(&mem, ub * units.size() + sizeof(BUnit) * units.size() + sizeof(long long) * count + 512) ==
-                cudaSuccess) {
-            p->bunits = (uint8_t*)mem;
-            p->d_units = (BUnit*)(p->bunits + ((ub * units.size() + 255) / 256) * 256);
-            p->d_bfirst = (long long*)((char*)p->d_units + ((sizeof(BUnit) * units.size() + 255) / 256) * 256);
-            p->n_units = (int)units.size();
-            ce = cudaMemcpy(p->d_units, units.data(), sizeof(BUnit) * units.size(), cudaMemcpyHostToDevice);
+        if (bu.size() < 0x7fffffffull && au.size() < 0x7fffffffull && cudaMalloc(&mem, total) == cudaSuccess) {
+            char* b = (char*)mem;
+            p->bunits = (uint8_t*)(b + oB);
+            p->d_units = (BUnit*)(b + oBu);
+            p->d_bfirst = (long long*)(b + oBf);
+            p->n_units = (int)bu.size();
+            if (!au.empty()) {
+                p->aunits = (uint8_t*)(b + oA);
+                p->d_aunits = (BUnit*)(b + oAu);
+                p->d_afirst = (long long*)(b + oAf);
+                p->n_aunits = (int)au.size();
+            }
+            ce = cudaMemcpy(p->d_units, bu.data(), sizeof(BUnit) * bu.size(), cudaMemcpyHostToDevice);
             if (ce == cudaSuccess)
-                ce = cudaMemcpy(p->d_bfirst, first.data(), sizeof(long long) * count, cudaMemcpyHostToDevice);
+                ce = cudaMemcpy(p->d_bfirst, bfirst.data(), sizeof(long long) * count, cudaMemcpyHostToDevice);
+            if (ce == cudaSuccess && !au.empty())
+                ce = cudaMemcpy(p->d_aunits, au.data(), sizeof(BUnit) * au.size(), cudaMemcpyHostToDevice);
+            if (ce == cudaSuccess && !au.empty())
+                ce = cudaMemcpy(p->d_afirst, afirst.data(), sizeof(long long) * count, cudaMemcpyHostToDevice);
             if (ce != cudaSuccess) {
                 cudaFree(mem);
                 cudaFree(p->dmem);
@@ -777,23 +915,21 @@ lrb_status create(int device, int sms, const lrb_gemm_desc* descs, size_t count,
     return LRB_OK;
 }
 
-cudaError_t launch(SplitPlan* p, cudaStream_t s) {
+// The pre-passes, then the main kernel.
+cudaError_t launch_with(SplitPlan* p, float* dump, cudaStream_t s) {
     if (p->bunits) {
-        cudaError_t e = slice_prec(p->precision, p->d_descs, p->d_units, p->n_units, p->bunits, s);
+        cudaError_t e = slice_prec(p->precision, false, p->d_descs, p->d_units, p->n_units, p->bunits, s);
+        if (e == cudaSuccess && p->aunits)
+            e = slice_prec(p->precision, true, p->d_descs, p->d_aunits, p->n_aunits, p->aunits, s);
         if (e != cudaSuccess) return e;
     }
-    return launch_prec(p->precision, p->d_descs, p->d_items, p->n_items, p->d_status, nullptr, p->test_stall,
-                       p->bunits, p->d_bfirst, s);
+    return launch_prec(p->precision, p->d_descs, p->d_items, p->n_items, p->bunits ? p->n_items_b : p->n_items,
+                       p->d_status, dump, p->test_stall, p->bunits, p->d_bfirst, p->aunits, p->d_afirst, s);
 }
 
-cudaError_t launch_dump(SplitPlan* p, float* dump, cudaStream_t s) {
-    if (p->bunits) {
-        cudaError_t e = slice_prec(p->precision, p->d_descs, p->d_units, p->n_units, p->bunits, s);
-        if (e != cudaSuccess) return e;
-    }
-    return launch_prec(p->precision, p->d_descs, p->d_items, p->n_items, p->d_status, dump, p->test_stall,
-                       p->bunits, p->d_bfirst, s);
-}
+cudaError_t launch(SplitPlan* p, cudaStream_t s) { return launch_with(p, nullptr, s); }
+
+cudaError_t launch_dump(SplitPlan* p, float* dump, cudaStream_t s) { return launch_with(p, dump, s); }
 
 int read_status(SplitPlan* p, cudaStream_t s, int* value) {
     cudaError_t e = cudaMemcpyAsync(value, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
