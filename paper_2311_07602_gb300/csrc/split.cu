@@ -806,6 +806,13 @@ int digit_count(int precision) {
     return (precision == LRB_PREC_SPLIT_BF16_S3 || precision == LRB_PREC_SPLIT_FP16_S3) ? 3 : 4;
 }
 
+// Entries whose A digit planes are made by the pre-pass: those with several
+// 64-column tiles, whose 128-row A tiles would otherwise be sliced once per
+// column tile.  (Pre-slicing A of single-column-tile entries too was measured
+// slower: 15.4 vs 14.0 ms on the 2048-entry T-form batch; the planes' extra
+// HBM traffic outweighs the integer work it moves out of the main kernel.)
+bool pre_a(const lrb_gemm_desc& d) { return d.n > kTN; }
+
 lrb_status create(int device, int sms, const lrb_gemm_desc* descs, size_t count, int precision, SplitPlan** out,
                   lrb_plan_info* info, int test_stall) {
     (void)device;
@@ -816,12 +823,12 @@ lrb_status create(int device, int sms, const lrb_gemm_desc* descs, size_t count,
     std::vector<SItem> items;
     for (int pass = 0; pass < 2; ++pass)
         for (size_t e = 0; e < count; ++e)
-            if ((descs[e].n > kTN) == (pass == 1))
+            if (pre_a(descs[e]) == (pass == 1))
                 for (int c0 = 0; c0 < descs[e].n; c0 += kTN)
                     for (int r0 = 0; r0 < descs[e].m; r0 += kTM) items.push_back(SItem{(int32_t)e, r0, c0, 0});
     size_t n_items_b = 0;
     for (size_t e = 0; e < count; ++e)
-        if (descs[e].n <= kTN) n_items_b += (size_t)((descs[e].m + kTM - 1) / kTM);
+        if (!pre_a(descs[e])) n_items_b += (size_t)((descs[e].n + kTN - 1) / kTN) * ((descs[e].m + kTM - 1) / kTM);
     if (items.size() > 0x7fffffffull) {
         set_last_error("too many split-precision tiles");
         return LRB_ERR_INVALID;
@@ -863,7 +870,7 @@ lrb_status create(int device, int sms, const lrb_gemm_desc* descs, size_t count,
             bfirst[e] = (long long)bu.size();
             for (int c0 = 0; c0 < descs[e].n; c0 += kTN)
                 for (int k0 = 0; k0 < descs[e].k; k0 += kc) bu.push_back(BUnit{(int32_t)e, c0, k0, 0});
-            if (descs[e].n > kTN) {
+            if (pre_a(descs[e])) {
                 afirst[e] = (long long)au.size();
                 for (int r0 = 0; r0 < descs[e].m; r0 += kTM)
                     for (int k0 = 0; k0 < descs[e].k; k0 += kc) au.push_back(BUnit{(int32_t)e, r0, k0, 0});
