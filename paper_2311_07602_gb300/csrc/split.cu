@@ -460,6 +460,31 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
         const int row = m0 + rloc;
         const bool row_ok = row < d.m;
         const int wc = min(kTN, d.n - n0);
+        {
+            // the CTA's next tile into L2 while this one runs: its C (one
+            // 128-byte line of 16 rows per thread) and, when pre-sliced, its
+            // first chunk's digit units
+            const int tn = t + gridDim.x;
+            if (tn < n_items) {
+                const SItem nx = items[tn];
+                const DevDesc dn = descs[nx.entry];
+                const int jj = tid >> 3, r = nx.row0 + 16 * (tid & 7);
+                if (jj < kTN && nx.col0 + jj < dn.n && r < dn.m)
+                    asm volatile("prefetch.global.L2 [%0];\n" ::"l"(dn.C + (size_t)r + (size_t)(nx.col0 + jj) * (size_t)dn.ldc));
+                if constexpr (MODE >= 1) {
+                    const int nchn = (dn.k + KC - 1) / KC;
+                    const uint8_t* ub = bunits + (size_t)(bfirst[nx.entry] + (long long)(nx.col0 / kTN) * nchn) * C_::unitB;
+                    for (int o = 128 * tid; o < C_::unitB; o += 128 * kThreadsS)
+                        asm volatile("prefetch.global.L2 [%0];\n" ::"l"(ub + o));
+                    if constexpr (MODE == 2) {
+                        const uint8_t* ua =
+                            aunits + (size_t)(afirst[nx.entry] + (long long)(nx.row0 / kTM) * nchn) * C_::unitA;
+                        for (int o = 128 * tid; o < C_::unitA; o += 128 * kThreadsS)
+                            asm volatile("prefetch.global.L2 [%0];\n" ::"l"(ua + o));
+                    }
+                }
+            }
+        }
         for (int c = 0; c < nch; ++c, ++iter) {
             const int stage = iter & 1;
             const int k0 = c * KC;
