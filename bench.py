@@ -730,6 +730,21 @@ def e2e_leg(L, handle, batches, flops, args, barrier, max_over_ranks, world, str
         d2h += 8 * C.numel()
         fl += sub.flops()
     descs = np.concatenate(rows)
+    # the box's pinned-copy bandwidth in this run (context for the e2e figure):
+    # the largest A buffer in, then out, each timed alone with CUDA events
+    big = max((h[0] for h in hold), key=lambda t: t.numel())
+    dbuf = torch.empty(big.numel(), dtype=torch.float64, device="cuda")
+    copy_gbs = {}
+    for name, dst, src in (("h2d", dbuf, big), ("d2h", big, dbuf)):
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        dst.copy_(src, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        copy_gbs[name] = round(8 * big.numel() / (e0.elapsed_time(e1) / 1e3) / 1e9, 1)
+    del dbuf
     torch.cuda.synchronize()
     for _ in range(args.warmup):
         handle.execute_host(descs, stream)
@@ -744,7 +759,7 @@ def e2e_leg(L, handle, batches, flops, args, barrier, max_over_ranks, world, str
     del hold
     return {"value": round(world * fl * args.e2e_steps / secs / 1e9, 2), "unit": UNIT,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps,
-            "flops_per_step_per_rank": fl,
+            "flops_per_step_per_rank": fl, "pinned_copy_gbs": copy_gbs,
             "api": "lrb_execute_host (pinned host buffers; copies in, compute and copies out pipelined in pieces)"}
 
 
