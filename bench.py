@@ -140,6 +140,46 @@ def cpu_baseline(fraction: float, nthreads: int = 0):
     return total_flops, total_s, used, entries
 
 
+def cpu_baseline_extras():
+    """The oracle, as it stands, on small samples of the other workloads
+    (same shapes and distributions), timed on the host cores: the paper's
+    low-rank chain (2000 blocks, b 1024, r 16; the paper's flop count), the
+    randomized SVD (4 kernel-matrix blocks, 1024^2, r 16, l 26, q 1; the
+    library's flop count) and the split-precision product (4 T-form entries,
+    1024 x 64 x 1024, BF16 S = 3; FP64-equivalent flops)."""
+    import oracle
+    from oracle import lowrank as OL
+    from paper_2311_07602_gb300 import workloads as W
+    out = {}
+    lb = W.lr_batch(2000, 1024, 16, seed=7016, device="cpu")
+    host = {k: t.numpy() for k, t in lb.bufs.items()}
+    t0 = time.perf_counter()
+    used = oracle.lr_chain_batch(host, lb.offs, lb.ra, lb.rb, lb.k)
+    dt = time.perf_counter() - t0
+    out["lr_chain"] = {"gflops_paper_count": round(lb.flops_paper() / dt / 1e9, 2), "threads": used,
+                       "sample": "2000 blocks, b 1024, r 16, N(0,1)"}
+    b, r, l, q, cnt = 1024, 16, 26, 1, 4
+    A = W.kernel_blocks(cnt, b, b, seed=7, device="cpu").numpy()
+    Om = W.gaussian_test_matrix(b, l, seed=8, device="cpu").numpy().reshape(l, b).T
+    t0 = time.perf_counter()
+    for e in range(cnt):
+        OL.rsvd(A[e * b * b:(e + 1) * b * b].reshape(b, b).T, Om, r, q)
+    dt = time.perf_counter() - t0
+    out["rsvd"] = {"gflops": round(cnt * OL.lowrank_flops(b, b, l, r, q) / dt / 1e9, 2),
+                   "blocks_per_s": round(cnt / dt, 1), "sample": f"{cnt} kernel-matrix blocks {b}x{b}, r {r}, l {l}, q {q}"}
+    rng = np.random.default_rng(4)
+    p = oracle.PRESETS["bf16_s3"]
+    t0 = time.perf_counter()
+    for _ in range(4):
+        Asp = rng.standard_normal((1024, 1024)) * 10.0 ** rng.uniform(-4, 4, (1024, 1024))
+        Bsp = rng.standard_normal((1024, 64)) * 10.0 ** rng.uniform(-4, 4, (1024, 64))
+        oracle.split_gemm(Asp, Bsp, np.zeros((1024, 64)), p)
+    dt = time.perf_counter() - t0
+    out["split_bf16_s3"] = {"gflops_fp64_equiv": round(4 * 2.0 * 1024 * 64 * 1024 / dt / 1e9, 3),
+                            "sample": "4 T-form entries 1024 x 64 x 1024, 10^U(-4,4) N(0,1) (single-threaded numpy)"}
+    return out
+
+
 def run_reference(args):
     rank, _, world = dist_env()
     if world > 1 and rank != 0:
@@ -314,6 +354,8 @@ def main():
         line["cpu_baseline"] = {"value": round(f / s / 1e9, 3), "unit": UNIT, "cores": used, "kind": "oracle",
                                 "sample": (f"first {args.cpu_fraction:.3g} of every group of the sweep "
                                            f"({ents} entries, {f:.3g} flops, {s:.1f} s on the host cores)")}
+        if not args.no_extras:
+            line["cpu_baseline"]["extras"] = cpu_baseline_extras()
     if plan is not None:
         plan.close()
     handle.close()
