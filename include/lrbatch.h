@@ -159,7 +159,7 @@ lrb_status lrb_plan_destroy(lrb_plan* p);
  * A, B and C into a handle-owned device arena (entries packed with tight
  * leading dimensions; runs of host-contiguous tight entries move in one copy;
  * an operand whose pointer and shape repeat an earlier entry's is copied
- * once), runs the batch in up to 16 pieces whose copies in, launches and
+ * once), runs the batch in up to 64 pieces whose copies in, launches and
  * copies out overlap on three streams (the layout and plans are cached and
  * reused while the shape list repeats), copies every C back and synchronises
  * `stream`.  Returns after host C holds the result.  Not thread-safe per
