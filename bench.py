@@ -671,9 +671,11 @@ def serving_leg(L, handle, dev, peak_fp64, budget=40 << 30):
     request: 1..512 products, b log-uniform [64, 2048], r in {8..128}, T/O
     50/50; operands are views into a 4 GB device pool, results go to a 64 GB
     device ring.  Offered loads: 0.25 / 0.5 / 0.75 / 0.9 x the FP64 capacity
-    (FP64 peak / mean request flops) for 3 s each, and the stated overload
-    rates 1,000 and 20,000 req/s for 0.5 s each (waiting FIFO limited to 32
-    so the backlog drains quickly); 40 GB admission budget, 4 stream slots."""
+    (FP64 peak / mean request flops) for 3 s each, the stated overload rates
+    1k / 2k / 5k / 10k / 20k req/s for 0.5 s each (waiting FIFO limited to 32
+    so the backlog drains quickly), and 0.9 x the FP64 capacity once more with
+    split-precision (BF16, S = 3) waves; 40 GB admission budget, 4 stream
+    slots."""
     import torch
     from paper_2311_07602_gb300 import workloads as W
     g = torch.Generator(device=dev)
@@ -683,12 +685,13 @@ def serving_leg(L, handle, dev, peak_fp64, budget=40 << 30):
     _, probe = W.serving_requests(2000, 1.0, seed=55)
     mean_flops = float(np.mean([np.sum(2.0 * bb.astype(np.float64) ** 2 * rr) for _, bb, rr in probe]))
     capacity = 0.98 * peak_fp64 * 1e12 / mean_flops
-    points = [(f"{fr:g}x capacity", fr * capacity, 3.0, 4096) for fr in (0.25, 0.5, 0.75, 0.9)]
-    points += [("1k req/s", 1000.0, 0.5, 32), ("20k req/s", 20000.0, 0.5, 32)]
+    points = [(f"{fr:g}x capacity", fr * capacity, 3.0, 4096, L.LRB_PREC_FP64) for fr in (0.25, 0.5, 0.75, 0.9)]
+    points += [(f"{r // 1000}k req/s", float(r), 0.5, 32, L.LRB_PREC_FP64) for r in (1000, 2000, 5000, 10000, 20000)]
+    points += [("0.9x FP64 capacity, split BF16 S=3 waves", 0.9 * capacity, 3.0, 4096, L.LRB_PREC_SPLIT_BF16_S3)]
     rng = np.random.default_rng(505)
     cursor = 0
     results = []
-    for idx, (label, rate, secs, max_waiting) in enumerate(points):
+    for idx, (label, rate, secs, max_waiting, prec) in enumerate(points):
         count = max(4, int(rate * secs))
         arrivals, reqs = W.serving_requests(count, rate, seed=500 + idx)
         descs = []
@@ -714,6 +717,7 @@ def serving_leg(L, handle, dev, peak_fp64, budget=40 << 30):
         torch.cuda.synchronize()
         q = L.Queue(handle, budget, max_inflight=4)
         q.set_limits(max_waiting)
+        q.set_precision(prec)
         tickets, codes = [], {}
         t0 = time.perf_counter()
         for t_arr, d in zip(arrivals, descs):
@@ -728,7 +732,8 @@ def serving_leg(L, handle, dev, peak_fp64, budget=40 << 30):
             q.wait(tk, 300000)
         st = q.stats()
         q.close()
-        results.append({"load": label, "offered_req_s": round(rate, 2), "duration_s": round(submit_s, 3),
+        results.append({"load": label, "precision": "fp64" if prec == L.LRB_PREC_FP64 else "split_bf16_s3",
+                        "offered_req_s": round(rate, 2), "duration_s": round(submit_s, 3),
                         "submitted": count, "accepted": int(st["accepted"]),
                         "rejected_queue_full": int(st["rejected_full"]), "rejected_budget": int(st["rejected_budget"]),
                         "completed": int(st["completed"]), "p50_ms": round(st["p50_ms"], 3),
