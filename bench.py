@@ -402,7 +402,7 @@ def extras(L, handle, stream, dev, peak_fp64, timed, which, split_batch, dmma_sc
 
 
 def lowrank_leg(L, handle, dev, peak_fp64, timed, count=1024, b=1024, r=16, p=10, q=1):
-    """Producers and consumers of low-rank blocks (Sec. 3): the randomized SVD
+    """Producers and consumers of low-rank blocks (Sec. 2): the randomized SVD
     of `count` dense b x b blocks of the Laplace kernel 1/|x - y| between two
     separated point clusters (the admissible blocks of a hierarchical matrix)
     to rank r with p oversampling columns and q power iterations; the

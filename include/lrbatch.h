@@ -6,7 +6,7 @@
  * Deshmukh, Yokota and Bosilca, "Cache Optimization and Performance Modeling
  * of Batched, Small, and Rectangular Matrix Multiplication on Intel, AMD, and
  * Fujitsu Processors" (arXiv 2311.07602):
- *   - a block of shape (m, n, rank) is stored as U S V (Eq. 1, Sec. 3);
+ *   - a block of shape (m, n, rank) is stored as U S V (Eq. 1, Sec. 2);
  *   - the low-rank product multiplies a "skinny" and a "small" matrix
  *     (Alg. 1; first step C_temp = A_{V^T} B_U), batched over many
  *     independent blocks (Alg. 2, loop 1 over the batch);
@@ -278,9 +278,9 @@ lrb_status lrb_queue_stats(lrb_queue* q, lrb_queue_stats_t* out);
 lrb_status lrb_queue_destroy(lrb_queue* q, int timeout_ms);
 
 /* ---- producers and consumers of low-rank blocks ---------------------------
- * A block of shape (m, n, rank) is stored as U S V (Eq. 1, Sec. 3) with a
+ * A block of shape (m, n, rank) is stored as U S V (Eq. 1, Sec. 2) with a
  * diagonal S: U is m x r (ldu >= m), S holds r values, V is r x n (ldv >= r);
- * device pointers, column-major.  Sec. 3 names the calls around the batched
+ * device pointers, column-major.  Sec. 2 names the calls around the batched
  * low-rank product: blocks are produced from dense ones by a randomized SVD
  * (Halko, Martinsson and Tropp), and the low-rank product is the first step
  * of the rounded addition of low-rank blocks.  Each call below plans a batch

@@ -5,11 +5,11 @@ benchmark's CPU-baseline leg; never by the library.  Plain numpy in binary64;
 numpy's matmul, QR and SVD serve as single steps, nothing is blocked, fused or
 reordered beyond the algorithms stated here.
 
-A block of shape (m, n, rank) is stored as A ~= U S V (Eq. 1, Sec. 3): U is
-m x r, S is r x r (here diagonal, given by its r values), V is r x n.  Sec. 3
+A block of shape (m, n, rank) is stored as A ~= U S V (Eq. 1, Sec. 2): U is
+m x r, S is r x r (here diagonal, given by its r values), V is r x n.  Sec. 2
 names the producers and consumers around the batched low-rank product:
 
-* randomized SVD (Sec. 3 cites Halko, Martinsson and Tropp, "Finding structure
+* randomized SVD (Sec. 2 cites Halko, Martinsson and Tropp, "Finding structure
   with randomness", 2009/2011) produces U, S, V from a dense block:
     - stage A, randomized range finder: Y = A Omega for an n x l Gaussian test
       matrix Omega (l = r + oversampling), Q = orthonormal basis of range(Y);
@@ -22,7 +22,7 @@ names the producers and consumers around the batched low-rank product:
   oracle and the GPU path see the same Omega.
 * expansion back to a dense block: D <- D + U diag(S) V (Eq. 1), computed as
   (U diag(S)) V: the columns of U scaled first, then one product.
-* rounded addition (Sec. 3 cites Bebendorf's stabilised rounded addition, whose
+* rounded addition (Sec. 2 cites Bebendorf's stabilised rounded addition, whose
   first step is the low-rank product): the sum of two low-rank blocks
   U1 S1 V1 + U2 S2 V2, truncated to rank r, by the standard route:
   Uc = [U1 diag(S1), U2 diag(S2)] = Q1 R1,  Vc^T = [V1; V2]^T = Q2 R2,

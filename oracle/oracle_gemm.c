@@ -9,7 +9,7 @@
  *
  * What it computes (paper: Alg. 1, first step C_temp = A_{V^T} * B_U, and the
  * per-entry loop nest of Alg. 2, loops 1-4, generalised to any m x n x k; the
- * low-rank factor shapes come from Eq. 1, the "(m, n, rank)" tuple of Sec. 3):
+ * low-rank factor shapes come from Eq. 1, the "(m, n, rank)" tuple of Sec. 2):
  *
  *   for every entry, for 0 <= i < m, 0 <= j < n:
  *       C[i + j*ldc] <- C[i + j*ldc] + sum_{p=0}^{k-1} A[i + p*lda] * B[p + j*ldb]
@@ -134,7 +134,7 @@ int oracle_max_threads(void)
 #endif
 }
 
-/* The low-rank multiplication core of Alg. 1 (Sec. 3): for low-rank blocks
+/* The low-rank multiplication core of Alg. 1 (Sec. 2): for low-rank blocks
  * A = A_U A_X A_{V^T} (rank ra) and B = B_U B_X B_{V^T} (rank rb),
  *     C_temp = A_{V^T} B_U     (ra x rb, k-long inner dimension)
  *     E_temp = A_X C_temp      (ra x rb)

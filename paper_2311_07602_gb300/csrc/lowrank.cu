@@ -1,12 +1,12 @@
-// Producers and consumers of low-rank blocks A ~= U diag(S) V (Eq. 1, Sec. 3),
+// Producers and consumers of low-rank blocks A ~= U diag(S) V (Eq. 1, Sec. 2),
 // batched over independent blocks like the low-rank product itself.
 //
-//  * randomized SVD (the producer Sec. 3 cites: Halko, Martinsson and Tropp):
+//  * randomized SVD (the producer Sec. 2 cites: Halko, Martinsson and Tropp):
 //    Y = A Omega, Q = orth(Y), q power iterations Q~ = orth(A^T Q),
 //    Q = orth(A Q~); then A^T Q = Q2 R2, R2^T = U~ Sigma W^T, U = Q U~_r,
 //    S = Sigma_r, V = W_r^T Q2^T (the SVD of B = Q^T A = R2^T Q2^T);
 //  * expansion D += (U diag(S)) V;
-//  * rounded addition (whose first step Sec. 3 says is the low-rank product):
+//  * rounded addition (whose first step Sec. 2 says is the low-rank product):
 //    [U1 S1, U2 S2] = Q1 R1, [V1; V2]^T = Q2 R2, R1 R2^T = U~ Sigma W^T,
 //    U = Q1 U~_r, S = Sigma_r, V = W_r^T Q2^T.
 //

@@ -5,7 +5,7 @@ buffers; it contains none of the multiplication's arithmetic, so both the
 GPU path and the CPU oracle can be fed from it.
 
 Shapes follow the low-rank setting of the paper: an (m, n, rank) block is
-U S V (Eq. 1, Sec. 3), so its products are the tall-skinny "T-form"
+U S V (Eq. 1, Sec. 2), so its products are the tall-skinny "T-form"
 C(b x r) += A(b x b) B(b x r) (dense block times a basis, e.g. the sampling
 step of a randomized SVD) and the outer "O-form" C(b x b) += A(b x r) B(r x b)
 (expanding U (S V) back to a dense block).  Values are N(0, 1) as in the
@@ -258,7 +258,7 @@ def lr_batch(batch: int, b: int, r: int, *, rb: int = None, seed: int = 0, devic
 
 
 # ---- dense blocks for the low-rank producers --------------------------------
-# Sec. 3: low-rank blocks come from dense blocks whose singular values decay
+# Sec. 2: low-rank blocks come from dense blocks whose singular values decay
 # fast, as the off-diagonal (admissible) blocks of hierarchical matrices do.
 # Stand-in: the Laplace kernel 1/|x - y| between two separated point clusters
 # (x uniform in the unit cube, y in the unit cube shifted by `sep` along the
