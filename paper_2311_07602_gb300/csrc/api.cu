@@ -754,8 +754,7 @@ lrb_status lrb_launch(lrb_plan* p, void* stream) {
         return e == cudaSuccess ? LRB_OK : cuda_fail(e, "low-rank chain launch");
     }
     if (p->lr_kind == 2) {
-        LRB_CUDA(cudaMemsetAsync(p->lr_work, 0, p->lr_work_bytes, s));
-        LRB_CUDA(launch_lr_zero(p->d_lr, p->lr_count, s));
+        // the three products write their outputs (overwrite form): nothing to clear
         for (lrb_plan* q : p->lr_stage) {
             lrb_status st = lrb_launch(q, stream);
             if (st != LRB_OK) return st;
@@ -1137,6 +1136,7 @@ lrb_status lrb_lr_plan_create(lrb_handle* h, const lrb_lr_desc* d, size_t count,
         lrb_plan_opts o = default_opts();
         o.use_graph = 1;
         o.check_alias = 0;
+        o.overwrite = 1;   // C_temp, E_temp and G are written, as Alg. 1 assigns them
         const std::vector<lrb_gemm_desc>* st[3] = {&s1, &s2, &s3};
         for (int i = 0; i < 3; ++i) {
             lrb_status r = lrb_plan_create(h, st[i]->data(), count, &o, &p->lr_stage[i]);

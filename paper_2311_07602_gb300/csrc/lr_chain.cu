@@ -223,20 +223,3 @@ cudaError_t launch_lr_chain(const LrDesc* d_descs, int count, int rmax, cudaStre
 
 }  // namespace lrb
 
-namespace lrb {
-namespace {
-// Zero every entry's G (ra x rb, leading dimension ldg): the unfused
-// comparator accumulates its last product into G.
-__global__ void k_lr_zero(const LrDesc* __restrict__ descs) {
-    const LrDesc d = descs[blockIdx.x];
-    for (int o = threadIdx.x; o < d.ra * d.rb; o += blockDim.x)
-        d.G[(size_t)(o % d.ra) + (size_t)(o / d.ra) * d.ldg] = 0.0;
-}
-}  // namespace
-
-cudaError_t launch_lr_zero(const LrDesc* d_descs, int count, cudaStream_t s) {
-    if (count <= 0) return cudaSuccess;
-    k_lr_zero<<<count, 128, 0, s>>>(d_descs);
-    return cudaGetLastError();
-}
-}  // namespace lrb

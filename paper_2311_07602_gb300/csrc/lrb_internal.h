@@ -78,7 +78,6 @@ int variant_set(int v);
 size_t lr_chain_smem_bytes_for(int stage);
 int lr_chain_max_rank();
 cudaError_t launch_lr_chain(const LrDesc* d_descs, int count, int rmax, cudaStream_t s);
-cudaError_t launch_lr_zero(const LrDesc* d_descs, int count, cudaStream_t s);
 
 // Sets the calling thread's lrb_last_error() message (api.cu).
 void set_last_error(const char* msg);
