@@ -339,13 +339,29 @@ __global__ void __launch_bounds__(kSvdThreads) k_jacobi_svd(const SvdDesc* __res
                 jacobi_pair(round, tid, L, p, q);
                 double c = 1.0, s = 0.0;
                 const double a = s_abg[3 * tid], b = s_abg[3 * tid + 1], g = s_abg[3 * tid + 2];
-                if (q < l && g != 0.0 && fabs(g) > tol * sqrt(a) * sqrt(b)) {
-                    // t = tan(theta) of the rotation that makes the pair orthogonal
-                    const double zeta = (b - a) / (2.0 * g);
-                    const double az = fabs(zeta);
-                    const double root = az < 1e100 ? sqrt(fma(az, az, 1.0)) : az;
-                    const double t = copysign(1.0 / (az + root), zeta);
-                    c = 1.0 / sqrt(fma(t, t, 1.0));
+                // rotate when |g| > tol sqrt(a b), tested as g^2 > tol^2 a b (no square roots)
+                if (q < l && g != 0.0 && g * g > a * (tol * tol * b)) {
+                    // t = tan(theta) of the rotation that makes the pair orthogonal,
+                    // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (b - a) / 2g.
+                    // The angle is taken in binary32 (the FP64 divisions and square
+                    // roots cost more of the FP64 pipe than the whole rotation); c and
+                    // s then come from t in binary64, c = 1/sqrt(1 + t^2), s = c t, so
+                    // the rotation is orthogonal to binary64 precision and an inexact
+                    // angle only leaves a residual that the next sweep removes.
+                    const float gf = (float)g, df = (float)(b - a);
+                    double t;
+                    if (fabsf(gf) >= 1e-30f && fabsf(gf) <= 1e30f && fabsf(df) <= 1e30f) {
+                        const float zf = df / (2.0f * gf);
+                        const float az = fabsf(zf);
+                        const float tf = az < 1e18f ? 1.0f / (az + sqrtf(fmaf(az, az, 1.0f))) : 0.5f / az;
+                        t = copysign((double)tf, (double)zf);
+                    } else {                                   // outside binary32's range: binary64
+                        const double zeta = (b - a) / (2.0 * g);
+                        const double az = fabs(zeta);
+                        const double root = az < 1e100 ? sqrt(fma(az, az, 1.0)) : az;
+                        t = copysign(1.0 / (az + root), zeta);
+                    }
+                    c = rsqrt(fma(t, t, 1.0));
                     s = c * t;
                     if (s != 0.0) s_rot[cur] = 1;
                 }
