@@ -445,6 +445,25 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
         }
     };
 
+    // Pre-sliced digit units of chunk cc of tile (entry, r0, c0) into stage stg:
+    // B's planes and column exponents, and (MODE 2) A's planes and row
+    // exponents, with 16-byte cp.async; one commit group.
+    auto copy_units = [&](int entry, int r0, int c0, int nch_e, int cc, int stg) {
+        uint8_t* pa = smem + stg * (S * (C_::planeA + C_::planeB));
+        uint8_t* pb = pa + S * C_::planeA;
+        if constexpr (MODE == 2) {
+            const uint8_t* src = aunits + (size_t)(afirst[entry] + (long long)(r0 / kTM) * nch_e + cc) * C_::unitA;
+            for (int o = 16 * tid; o < S * C_::planeA; o += 16 * kThreadsS) cp_async16(pa + o, src + o);
+            if (tid < kTM / 4) cp_async16(&s_E[stg][4 * tid], src + S * C_::planeA + 16 * tid);
+        }
+        if constexpr (MODE >= 1) {
+            const uint8_t* src = bunits + (size_t)(bfirst[entry] + (long long)(c0 / kTN) * nch_e + cc) * C_::unitB;
+            for (int o = 16 * tid; o < S * C_::planeB; o += 16 * kThreadsS) cp_async16(pb + o, src + o);
+            if (tid < kTN / 4) cp_async16(&s_F[stg][4 * tid], src + S * C_::planeB + 16 * tid);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+
     int iter = 0;
     int last_commit = -1;     // iteration of the most recent tensor-core commit
     int t = blockIdx.x;
@@ -493,18 +512,12 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
             uint8_t* planeB = planeA + S * C_::planeA;
             constexpr bool pre = PRE;
             constexpr bool preA = MODE == 2;
-            if constexpr (preA) {
-                const uint8_t* src = aunits + (size_t)(afirst[item.entry] + (long long)(m0 / kTM) * nch + c) * C_::unitA;
-                for (int o = 16 * tid; o < S * C_::planeA; o += 16 * kThreadsS) cp_async16(planeA + o, src + o);
-                if (tid < kTM / 4) cp_async16(&s_E[stage][4 * tid], src + S * C_::planeA + 16 * tid);
-                asm volatile("cp.async.commit_group;\n" ::: "memory");
-            }
+            // (0) pre-sliced units.  MODE 1 copies this chunk's B here, where the
+            // copy overlaps the loads and slicing of A; MODE 2 (nothing else to
+            // overlap) copies the next chunk's units one iteration ahead (step 6),
+            // so only the CTA's first chunk copies its own here.
             if constexpr (PRE) {
-                // (0) this chunk's pre-sliced B: planes and exponents, 16 bytes per copy
-                const uint8_t* src = bunits + (size_t)(bfirst[item.entry] + (long long)(n0 / kTN) * nch + c) * C_::unitB;
-                for (int o = 16 * tid; o < S * C_::planeB; o += 16 * kThreadsS) cp_async16(planeB + o, src + o);
-                if (tid < kTN / 4) cp_async16(&s_F[stage][4 * tid], src + S * C_::planeB + 16 * tid);
-                asm volatile("cp.async.commit_group;\n" ::: "memory");
+                if (MODE == 1 || iter == 0) copy_units(item.entry, m0, n0, nch, c, stage);
             }
             // (1) loads: A row `row`, chunk columns [q QC, q QC + QC); B columns 4 w .. 4 w + 3
             double av[preA ? 1 : QC];
@@ -671,6 +684,16 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
                     load_c0(d, m0, n0);   // chunk c is chunk 0 of this tile; consumed next iteration
                 }
             }
+            // (6) MODE 2: the next chunk's units into the other stage, which the
+            // recombination just finished with (and the MMAs that read it are done)
+            if constexpr (MODE == 2) {
+                if (c + 1 < nch) {
+                    copy_units(item.entry, m0, n0, nch, c + 1, stage ^ 1);
+                } else if (t + (int)gridDim.x < n_items) {
+                    const SItem nx = items[t + gridDim.x];
+                    copy_units(nx.entry, nx.row0, nx.col0, (descs[nx.entry].k + KC - 1) / KC, 0, stage ^ 1);
+                }
+            }
             prev.C = d.C;
             prev.m = d.m;
             prev.n = d.n;
@@ -697,6 +720,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
             mbar_wait(smem_u32(&s_bar[last_commit & 1]), (uint32_t)((last_commit >> 1) & 1));
         if (tid == 0) atomicExch(status, 1);
     }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // no copy may land after the CTA exits
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
