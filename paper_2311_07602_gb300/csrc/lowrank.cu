@@ -59,9 +59,8 @@ struct PackDesc {          // dst = [src1 diag(s1), src2 diag(s2)] or its transp
 
 constexpr int kQrThreads = 512;
 constexpr int kQrWarps = kQrThreads / 32;
-constexpr int kSvdThreads = 512;
+constexpr int kSvdMaxThreads = 512;
 constexpr int kMaxSweeps = 40;
-constexpr int kMaxPairs = (LRB_LR_MAX_L + 1) / 2;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -258,34 +257,81 @@ __device__ __forceinline__ void jacobi_pair(int round, int k, int L, int& p, int
     }
 }
 
-// One-sided Jacobi SVD (Hestenes) of the small matrix M = X Y^T, one CTA per
-// matrix, M and the accumulated rotations W in shared memory.  A sweep
-// visits every column pair once in round-robin order (l/2 disjoint pairs per
-// round).  A round has three phases, laid out so that no FP64 operation is
-// repeated across lanes (the FP64 pipe is the cost): the three dot products
-// of every pair (T lanes per pair, T the largest power of two with
-// pairs x T <= 32), the rotation of every pair by one lane, and the
-// rotations applied with one lane per (pair, row).  A pair is rotated when
-// |m_p . m_q| > tol ||m_p|| ||m_q||.  At convergence M W = U~ Sigma with
-// orthogonal columns: sigma_c = ||M(:, c)||, U~(:, c) = M(:, c) / sigma_c
-// (zero when sigma_c = 0), written in descending order of sigma.  A sweep
-// limit bounds the iteration; hitting it sets the status word and writes the
-// last iterate.
-__global__ void __launch_bounds__(kSvdThreads) k_jacobi_svd(const SvdDesc* __restrict__ descs,
-                                                           int* __restrict__ status) {
+// Lanes per column pair in k_jacobi_svd: the power of two T <= 32, with
+// pairs x T <= limit threads, that minimises a round's FP64 instructions on
+// the busiest SM sub-partition.  A warp instruction holds the FP64 pipe for
+// the same time whatever the number of active lanes, so a round costs each
+// working warp 11 ceil(l / T) instructions (3 dot-product FMAs and 8
+// rotation operations per row a lane owns), 3 log2 T (the butterfly sums)
+// and about 12 (the rotation angle), and warps w, w + 4, ... share one
+// sub-partition.
+__host__ __device__ inline int jacobi_lanes(int l, int limit) {
+    const int np = ((l + 1) & ~1) / 2;
+    int best = 1, best_cost = 0x7fffffff;
+    for (int T = 1, lg = 0; T <= 32 && np * T <= limit; T *= 2, ++lg) {
+        const int warps = (np * T + 31) / 32;
+        const int cost = ((warps + 3) / 4) * (11 * ((l + T - 1) / T) + 3 * lg + 12);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = T;
+        }
+    }
+    return best;
+}
+
+// Threads of a k_jacobi_svd launch whose matrices have l <= maxl.
+int jacobi_threads(int maxl) {
+    int t = 32;
+    for (int l = 2; l <= maxl; ++l) {
+        const int np = ((l + 1) & ~1) / 2;
+        t = std::max(t, (np * jacobi_lanes(l, kSvdMaxThreads) + 31) / 32 * 32);
+    }
+    return t;
+}
+
+// SVD of the small matrix M = X Y^T, one CTA per matrix, everything in
+// shared memory (leading dimension lm = l | 1: odd, so that lanes on one row
+// of different columns hit different banks).
+//
+// Preconditioning (Drmac and Veselic, "New fast and accurate Jacobi SVD
+// algorithm", 2008): a Householder QR with column pivoting (Businger and
+// Golub), M P = Q R, and the one-sided Jacobi method then runs on R^T, whose
+// columns are much closer to orthogonal; cores of rounded additions, sums of
+// two graded spectra, need about a third fewer rotations that way.  Column j
+// of the QR takes the remaining column of largest norm (smallest index on
+// ties); one thread owns each column (lanes = columns), so a reflector's dot
+// products and updates cost one warp instruction per row for 32 columns.
+//
+// One-sided Jacobi (Hestenes) on X = R^T: a sweep visits every column pair
+// once in round-robin order (l/2 disjoint pairs per round).  A group of T
+// lanes (jacobi_lanes) owns one pair of a round: each lane sums the three dot
+// products over its rows, a butterfly gives every lane of the group the same
+// sums (the same two partials are added at each step, in either order),
+// every lane derives the same rotation, and each lane rotates its rows of X
+// and of the accumulated rotations V.  Pairs of a round touch disjoint
+// columns, so a round needs one barrier.  A pair is rotated when
+// |x_p . x_q| > tol ||x_p|| ||x_q||.  At convergence X V = U_x Sigma with
+// orthogonal columns, so M = (Q V) Sigma (P U_x)^T: sigma_c = ||X(:, c)||,
+// the left singular vectors are Q V (Q applied to V by its reflectors), the
+// right ones P U_x with U_x(:, c) = X(:, c) / sigma_c (zero when sigma_c =
+// 0); both are written in descending order of sigma.  A sweep limit bounds
+// the iteration; hitting it sets the status word and writes the last iterate.
+__global__ void __launch_bounds__(kSvdMaxThreads) k_jacobi_svd(const SvdDesc* __restrict__ descs,
+                                                              int* __restrict__ status) {
     extern __shared__ __align__(16) double sm[];
-    __shared__ double s_abg[3 * kMaxPairs];
-    __shared__ double s_cs[2 * kMaxPairs];
     __shared__ int s_rot[2];
     const SvdDesc d = descs[blockIdx.x];
-    const int l = d.l;
-    double* M = sm;                 // l x l, ld l
-    double* W = sm + l * l;         // l x l
-    double* sg = W + l * l;         // l
-    int* perm = reinterpret_cast<int*>(sg + l);
-    const int tid = threadIdx.x;
+    const int l = d.l, lm = l | 1;
+    double* M = sm;                 // M, then R, then X = R^T; l x l, ld lm
+    double* V = M + l * lm;         // accumulated rotations
+    double* H = V + l * lm;         // reflectors below the diagonal (v_j(j) = 1 implied)
+    double* sg = H + l * lm;        // squared trailing column norms, later sigma
+    double* tau = sg + l;
+    int* perm = reinterpret_cast<int*>(tau + l);
+    int* piv = perm + l;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
 
-    for (int e = tid; e < l * l; e += kSvdThreads) {
+    for (int e = tid; e < l * l; e += nt) {
         const int i = e % l, c = e / l;
         double s;
         if (d.X != nullptr) {
@@ -294,94 +340,168 @@ __global__ void __launch_bounds__(kSvdThreads) k_jacobi_svd(const SvdDesc* __res
         } else {
             s = d.Y[c + i * l];
         }
-        M[e] = s;
-        W[e] = i == c ? 1.0 : 0.0;
+        M[i + c * lm] = s;
+        V[i + c * lm] = i == c ? 1.0 : 0.0;
     }
+    // Column c of the QR belongs to lane c % 32 of warp (w0 + c / 32) % nw; w0
+    // varies with the CTA so that the CTAs on one SM spread this serial work
+    // over the SM's sub-partitions.
+    const int w0 = (int)(blockIdx.x % (unsigned)nw);
+    const int cown = lane + 32 * ((warp - w0 + nw) % nw);
+    __syncthreads();
+    if (cown < l) {
+        double s = 0.0;
+        for (int i = 0; i < l; ++i) s = fma(M[i + cown * lm], M[i + cown * lm], s);
+        sg[cown] = s;
+        piv[cown] = cown;
+    }
+    __syncthreads();
+    for (int j = 0; j < l; ++j) {
+        if (warp == w0) {
+            // pivot: the largest remaining norm (non-negative doubles order like their bit patterns)
+            long long best = -1;
+            int bi = j;
+            for (int c = j + lane; c < l; c += 32) {
+                const long long v = __double_as_longlong(sg[c]);
+                if (v > best) {
+                    best = v;
+                    bi = c;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) {
+                    best = ob;
+                    bi = oi;
+                }
+            }
+            if (bi != j) {
+                for (int i = lane; i < l; i += 32) {
+                    const double t = M[i + j * lm];
+                    M[i + j * lm] = M[i + bi * lm];
+                    M[i + bi * lm] = t;
+                }
+                if (lane == 0) {
+                    const double t = sg[j];
+                    sg[j] = sg[bi];
+                    sg[bi] = t;
+                    const int p = piv[j];
+                    piv[j] = piv[bi];
+                    piv[bi] = p;
+                }
+            }
+            __syncwarp();
+            // reflector of column j: H_j = I - tau v v^T maps M(j:l, j) to beta e_j
+            const double alpha = M[j + j * lm];
+            double s2 = 0.0;
+            for (int i = j + 1 + lane; i < l; i += 32) s2 = fma(M[i + j * lm], M[i + j * lm], s2);
+            s2 = warp_sum(s2);
+            double t = 0.0, scal = 0.0, beta = alpha;
+            if (s2 > 0.0) {
+                beta = -copysign(hypot(alpha, sqrt(s2)), alpha);
+                t = (beta - alpha) / beta;
+                scal = 1.0 / (alpha - beta);
+            }
+            for (int i = j + 1 + lane; i < l; i += 32) {
+                H[i + j * lm] = M[i + j * lm] * scal;
+                M[i + j * lm] = 0.0;
+            }
+            if (lane == 0) {
+                M[j + j * lm] = beta;
+                tau[j] = t;
+            }
+        }
+        __syncthreads();
+        if (cown > j && cown < l) {
+            double* x = M + cown * lm;
+            const double* v = H + j * lm;
+            double w = x[j];
+            for (int i = j + 1; i < l; ++i) w = fma(v[i], x[i], w);
+            const double tw = tau[j] * w;
+            x[j] -= tw;
+            double s = 0.0;
+            for (int i = j + 1; i < l; ++i) {
+                const double y = fma(-tw, v[i], x[i]);
+                x[i] = y;
+                s = fma(y, y, s);
+            }
+            sg[cown] = s;
+        }
+        __syncthreads();
+    }
+    // X = R^T, in place
+    for (int e = tid; e < l * l; e += nt) {
+        const int i = e % l, c = e / l;
+        if (i < c) {
+            const double t = M[i + c * lm];
+            M[i + c * lm] = M[c + i * lm];
+            M[c + i * lm] = t;
+        }
+    }
+    __syncthreads();
+
     const double tol = (double)l * 2.220446049250313e-16;   // l x 2^-52
     const int L = (l + 1) & ~1;                              // players, with a bye for odd l
     const int NP = L / 2;                                    // pairs per round
-    int T = 1;
-    while (2 * T * NP <= 32) T *= 2;
-    const int dot_warps = (NP * T + 31) / 32;
+    const int T = jacobi_lanes(l, nt);
+    const int k = tid / T, g = tid % T;                      // pair group, lane within it
     bool converged = false;
     for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
         const int cur = sweep & 1;
         if (tid == 0) s_rot[cur] = 0;
         __syncthreads();
         for (int round = 0; round < L - 1; ++round) {
-            if ((tid >> 5) < dot_warps) {           // whole warps, so the shuffles see every lane
-                const int k = tid / T, g = tid % T;
-                int p = 0, q = l;
-                if (k < NP) jacobi_pair(round, k, L, p, q);
-                double a = 0.0, b = 0.0, gm = 0.0;
-                if (q < l) {
+            int p = 0, q = l;
+            if (k < NP) jacobi_pair(round, k, L, p, q);
+            double a = 0.0, b = 0.0, gm = 0.0;
+            if (q < l) {
+                for (int i = g; i < l; i += T) {
+                    const double mp = M[i + p * lm], mq = M[i + q * lm];
+                    a = fma(mp, mp, a);
+                    b = fma(mq, mq, b);
+                    gm = fma(mp, mq, gm);
+                }
+            }
+            for (int o = T >> 1; o > 0; o >>= 1) {   // every lane of the warp takes part
+                a += __shfl_xor_sync(0xffffffffu, a, o);
+                b += __shfl_xor_sync(0xffffffffu, b, o);
+                gm += __shfl_xor_sync(0xffffffffu, gm, o);
+            }
+            // rotate when |g| > tol sqrt(a b), tested as g^2 > tol^2 a b (no square roots)
+            if (q < l && gm != 0.0 && gm * gm > a * (tol * tol * b)) {
+                // t = tan(theta) of the rotation that makes the pair orthogonal,
+                // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (b - a) / 2g.
+                // The angle is taken in binary32 (the FP64 divisions and square
+                // roots cost more of the FP64 pipe than the whole rotation); c and
+                // s then come from t in binary64, c = 1/sqrt(1 + t^2), s = c t, so
+                // the rotation is orthogonal to binary64 precision and an inexact
+                // angle only leaves a residual that the next sweep removes.
+                const float gf = (float)gm, df = (float)(b - a);
+                const float zf = df / (2.0f * gf);
+                double t;
+                if (fabsf(gf) >= 1e-30f && fabsf(gf) <= 1e30f && fabsf(df) <= 1e30f && fabsf(zf) < 1e18f) {
+                    const float az = fabsf(zf);
+                    t = copysign((double)(1.0f / (az + sqrtf(fmaf(az, az, 1.0f)))), (double)zf);
+                } else {                        // zeta or its parts outside binary32's range: binary64
+                    const double zeta = (b - a) / (2.0 * gm);
+                    const double az = fabs(zeta);
+                    const double root = az < 1e100 ? sqrt(fma(az, az, 1.0)) : az;
+                    t = copysign(1.0 / (az + root), zeta);
+                }
+                const double c = rsqrt(fma(t, t, 1.0));
+                const double s = c * t;
+                if (s != 0.0) {
                     for (int i = g; i < l; i += T) {
-                        const double mp = M[i + p * l], mq = M[i + q * l];
-                        a = fma(mp, mp, a);
-                        b = fma(mq, mq, b);
-                        gm = fma(mp, mq, gm);
+                        const double mp = M[i + p * lm], mq = M[i + q * lm];
+                        M[i + p * lm] = c * mp - s * mq;
+                        M[i + q * lm] = s * mp + c * mq;
+                        const double wp = V[i + p * lm], wq = V[i + q * lm];
+                        V[i + p * lm] = c * wp - s * wq;
+                        V[i + q * lm] = s * wp + c * wq;
                     }
+                    if (g == 0) s_rot[cur] = 1;
                 }
-                for (int o = T >> 1; o > 0; o >>= 1) {
-                    a += __shfl_xor_sync(0xffffffffu, a, o);
-                    b += __shfl_xor_sync(0xffffffffu, b, o);
-                    gm += __shfl_xor_sync(0xffffffffu, gm, o);
-                }
-                if (g == 0 && k < NP) {
-                    s_abg[3 * k] = a;
-                    s_abg[3 * k + 1] = b;
-                    s_abg[3 * k + 2] = gm;
-                }
-            }
-            __syncthreads();
-            if (tid < NP) {
-                int p, q;
-                jacobi_pair(round, tid, L, p, q);
-                double c = 1.0, s = 0.0;
-                const double a = s_abg[3 * tid], b = s_abg[3 * tid + 1], g = s_abg[3 * tid + 2];
-                // rotate when |g| > tol sqrt(a b), tested as g^2 > tol^2 a b (no square roots)
-                if (q < l && g != 0.0 && g * g > a * (tol * tol * b)) {
-                    // t = tan(theta) of the rotation that makes the pair orthogonal,
-                    // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (b - a) / 2g.
-                    // The angle is taken in binary32 (the FP64 divisions and square
-                    // roots cost more of the FP64 pipe than the whole rotation); c and
-                    // s then come from t in binary64, c = 1/sqrt(1 + t^2), s = c t, so
-                    // the rotation is orthogonal to binary64 precision and an inexact
-                    // angle only leaves a residual that the next sweep removes.
-                    const float gf = (float)g, df = (float)(b - a);
-                    double t;
-                    if (fabsf(gf) >= 1e-30f && fabsf(gf) <= 1e30f && fabsf(df) <= 1e30f) {
-                        const float zf = df / (2.0f * gf);
-                        const float az = fabsf(zf);
-                        const float tf = az < 1e18f ? 1.0f / (az + sqrtf(fmaf(az, az, 1.0f))) : 0.5f / az;
-                        t = copysign((double)tf, (double)zf);
-                    } else {                                   // outside binary32's range: binary64
-                        const double zeta = (b - a) / (2.0 * g);
-                        const double az = fabs(zeta);
-                        const double root = az < 1e100 ? sqrt(fma(az, az, 1.0)) : az;
-                        t = copysign(1.0 / (az + root), zeta);
-                    }
-                    c = rsqrt(fma(t, t, 1.0));
-                    s = c * t;
-                    if (s != 0.0) s_rot[cur] = 1;
-                }
-                s_cs[2 * tid] = c;
-                s_cs[2 * tid + 1] = s;
-            }
-            __syncthreads();
-            for (int e = tid; e < NP * l; e += kSvdThreads) {
-                const int k = e / l, i = e % l;
-                const double s = s_cs[2 * k + 1];
-                if (s == 0.0) continue;
-                const double c = s_cs[2 * k];
-                int p, q;
-                jacobi_pair(round, k, L, p, q);
-                const double mp = M[i + p * l], mq = M[i + q * l];
-                M[i + p * l] = c * mp - s * mq;
-                M[i + q * l] = s * mp + c * mq;
-                const double wp = W[i + p * l], wq = W[i + q * l];
-                W[i + p * l] = c * wp - s * wq;
-                W[i + q * l] = s * wp + c * wq;
             }
             __syncthreads();
         }
@@ -390,29 +510,43 @@ __global__ void __launch_bounds__(kSvdThreads) k_jacobi_svd(const SvdDesc* __res
             break;
         }
     }
-    for (int c = tid; c < l; c += kSvdThreads) {
+    for (int c = tid; c < l; c += nt) {
         double s = 0.0;
-        for (int i = 0; i < l; ++i) s = fma(M[i + c * l], M[i + c * l], s);
+        for (int i = 0; i < l; ++i) s = fma(M[i + c * lm], M[i + c * lm], s);
         sg[c] = sqrt(s);
     }
+    // Q V: the reflectors applied to each column of V, the last one first
+    if (cown < l) {
+        double* x = V + cown * lm;
+        for (int j = l - 1; j >= 0; --j) {
+            const double tj = tau[j];
+            if (tj == 0.0) continue;
+            const double* v = H + j * lm;
+            double w = x[j];
+            for (int i = j + 1; i < l; ++i) w = fma(v[i], x[i], w);
+            const double tw = tj * w;
+            x[j] -= tw;
+            for (int i = j + 1; i < l; ++i) x[i] = fma(-tw, v[i], x[i]);
+        }
+    }
     __syncthreads();
-    for (int c = tid; c < l; c += kSvdThreads) {
+    for (int c = tid; c < l; c += nt) {
         int rank = 0;
         for (int o = 0; o < l; ++o) rank += (sg[o] > sg[c] || (sg[o] == sg[c] && o < c)) ? 1 : 0;
         perm[rank] = c;
     }
     __syncthreads();
-    for (int e = tid; e < l * l; e += kSvdThreads) {
-        const int i = e % l, k = e / l;
-        const int c = perm[k];
+    for (int e = tid; e < l * l; e += nt) {
+        const int i = e % l, j = e / l;
+        const int c = perm[j];
         const double s = sg[c];
-        d.Ut[e] = s > 0.0 ? M[i + c * l] / s : 0.0;
-        d.W[e] = W[i + c * l];
+        d.Ut[i + j * l] = V[i + c * lm];
+        d.W[piv[i] + j * l] = s > 0.0 ? M[i + c * lm] / s : 0.0;
     }
-    for (int k = tid; k < l; k += kSvdThreads) {
-        const double s = sg[perm[k]];
-        d.sig[k] = s;
-        if (k < d.r) d.S[k] = s;
+    for (int j = tid; j < l; j += nt) {
+        const double s = sg[perm[j]];
+        d.sig[j] = s;
+        if (j < d.r) d.S[j] = s;
     }
     if (!converged && tid == 0) atomicOr(status, 1);
 }
@@ -460,7 +594,10 @@ __global__ void __launch_bounds__(256) k_pack_rows_t(const PackDesc* __restrict_
     }
 }
 
-size_t svd_smem(int l) { return (2 * (size_t)l * l + l) * 8 + (size_t)l * 4 + 16; }
+size_t svd_smem(int l) {
+    const size_t lm = (size_t)(l | 1);
+    return (3 * lm * l + 2 * (size_t)l) * 8 + 2 * (size_t)l * 4 + 16;
+}
 
 // ---------------------------------------------------------------- plans
 
@@ -583,6 +720,7 @@ struct Step {
     size_t smem;
     lrb_plan* g;
     bool panel = false;   // QR: the panel is staged in shared memory
+    int threads = 0;      // SVD: threads per CTA
 };
 
 // Dynamic shared memory a QR CTA may take beyond its static arrays.
@@ -644,7 +782,7 @@ lrb_status finish(LrPlan* p, Uploader& up, const std::vector<Step>& steps) {
                 le = cudaGetLastError();
                 break;
             case Step::kSvd:
-                k_jacobi_svd<<<s.count, kSvdThreads, s.smem, p->cap>>>(at<SvdDesc>(p->dmem, s.off), p->d_status);
+                k_jacobi_svd<<<s.count, s.threads, s.smem, p->cap>>>(at<SvdDesc>(p->dmem, s.off), p->d_status);
                 le = cudaGetLastError();
                 break;
             case Step::kPack:
@@ -785,7 +923,7 @@ lrb_status create_rsvd(lrb_handle* h, const lrb_rsvd_desc* d, size_t count, int 
     }
     steps.push_back({Step::kGemm, 0, 0, 0, pATY});
     steps.push_back(qr_step(oZR, c, maxn, maxl, limit));
-    steps.push_back({Step::kSvd, oS, c, svd_smem(maxl), nullptr});
+    steps.push_back({Step::kSvd, oS, c, svd_smem(maxl), nullptr, false, jacobi_threads(maxl)});
     steps.push_back({Step::kGemm, 0, 0, 0, pU});
     steps.push_back({Step::kGemm, 0, 0, 0, pV});
     if ((s = finish(p, up, steps)) != LRB_OK) return bail(s);
@@ -947,7 +1085,7 @@ lrb_status create_round_add(lrb_handle* h, const lrb_round_add_desc* d, size_t c
                             {Step::kPackT, oPV, c, 0, nullptr},
                             qr_step(oQ1, c, maxm, maxl, limit),
                             qr_step(oQ2, c, maxn, maxl, limit),
-                            {Step::kSvd, oS, c, svd_smem(maxl), nullptr},
+                            {Step::kSvd, oS, c, svd_smem(maxl), nullptr, false, jacobi_threads(maxl)},
                             {Step::kGemm, 0, 0, 0, pU},
                             {Step::kGemm, 0, 0, 0, pV}};
     if ((s = finish(p, up, steps)) != LRB_OK) return bail(s);

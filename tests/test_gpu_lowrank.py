@@ -14,7 +14,8 @@
   size on sampled entries, where the GPU's error must match the oracle's;
 * expansion: bitwise on integer data, Higham's bound on random data;
 * rounded addition: exact singular values of sums built from disjoint parts
-  of one orthonormal pair, reconstruction within 1e-11 of the oracle's.
+  of one orthonormal pair, reconstruction within 1e-11 of the oracle's, and
+  two parts 1e-28 apart (rotations outside binary32's range).
 Tolerances: the oracle and the GPU take the same steps with different
 summation orders and a different (but backward-stable) QR and SVD; with a
 gap g = sigma_r / sigma_{r+1} >= 100 the rank-r truncation moves by about
@@ -364,6 +365,25 @@ def test_round_add_known_spectrum(handle):
         Uo, So, Vo = OL.lr_round_add(*x, *y, r)
         assert np.linalg.norm((U * S) @ V - (Uo * So) @ Vo) <= 1e-12 * allv[0] * np.sqrt(r)
         check_factors(U, S, V)
+
+
+def test_round_add_extremely_graded_spectrum(handle):
+    """Two blocks 28 orders of magnitude apart.  The SVD core's QR leaves
+    columns whose norms differ by ~1e-28, where zeta = (b - a) / 2g of a
+    rotation is far outside binary32's range; such pairs must still be
+    rotated (in binary64), or V keeps rows at an O(1) angle."""
+    rng = np.random.default_rng(33)
+    m, n, r1, r2 = 120, 90, 10, 6
+    P, Q = orthonormal(rng, m, r1 + r2), orthonormal(rng, n, r1 + r2)
+    x = (P[:, :r1], np.logspace(0, -2, r1), Q[:, :r1].T.copy())
+    y = (P[:, r1:], 1e-28 * np.logspace(0, -2, r2), Q[:, r1:].T.copy())
+    r = r1 + r2
+    (U, S, V), = round_add_gpu(handle, [(x, y, r)])
+    check_factors(U, S, V)
+    allv = np.sort(np.concatenate([x[1], y[1]]))[::-1]
+    assert np.abs(S - allv).max() <= 1e-13
+    dense = (x[0] * x[1]) @ x[2] + (y[0] * y[1]) @ y[2]
+    assert np.linalg.norm((U * S) @ V - dense) <= 1e-13 * np.linalg.norm(dense)
 
 
 def test_round_add_random_matches_oracle(handle):
