@@ -146,10 +146,11 @@ __device__ __forceinline__ void reflect_column(const double* __restrict__ v, dou
 // column (a warp per trailing column).  Then R is copied out and
 // Q = H_0 ... H_{cols-1} [I; 0] is formed in place, backwards.  A zero column
 // gives tau = 0 (H = I), so rank-deficient input still yields an orthonormal
-// Q.  SMEM: the whole panel is staged in shared memory (rows x (cols + 1)
-// doubles with v), else it is worked on in place in global memory (L2).
-template <bool SMEM>
-__global__ void __launch_bounds__(kQrThreads, 1) k_house_qr(const QrDesc* __restrict__ descs) {
+// Q.  The matrix is worked on in place in global memory (the panels of the
+// resident CTAs stay in L2), the current reflector in shared memory; two CTAs
+// per SM fill each other's barrier and scalar phases.  (Staging a whole panel
+// in shared memory leaves room for one CTA per SM and measured slower.)
+__global__ void __launch_bounds__(kQrThreads, 2) k_house_qr(const QrDesc* __restrict__ descs) {
     extern __shared__ __align__(16) double sm[];
     __shared__ double red[kQrThreads + 1];
     __shared__ double s_tau[LRB_LR_MAX_L];
@@ -159,13 +160,7 @@ __global__ void __launch_bounds__(kQrThreads, 1) k_house_qr(const QrDesc* __rest
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double* v = sm;
     double* P = d.Y;
-    size_t ld = (size_t)d.ldy;
-    if constexpr (SMEM) {
-        P = sm + m;
-        for (int e = tid; e < m * l; e += kQrThreads) P[e] = d.Y[(size_t)(e % m) + (size_t)(e / m) * ld];
-        ld = (size_t)m;
-        __syncthreads();
-    }
+    const size_t ld = (size_t)d.ldy;
 
     for (int j = 0; j < l; ++j) {
         double* x = P + (size_t)j * ld;
@@ -239,9 +234,6 @@ __global__ void __launch_bounds__(kQrThreads, 1) k_house_qr(const QrDesc* __rest
             for (int c = j + 1 + warp; c < l; c += kQrWarps) reflect_column(v, P + (size_t)c * ld, j, m, tau, lane);
         for (int i = tid; i < m; i += kQrThreads) x[i] = i < j ? 0.0 : (i == j ? 1.0 - tau : -tau * v[i]);
         __syncthreads();
-    }
-    if constexpr (SMEM) {
-        for (int e = tid; e < m * l; e += kQrThreads) d.Y[(size_t)(e % m) + (size_t)(e / m) * (size_t)d.ldy] = P[e];
     }
 }
 
@@ -719,37 +711,18 @@ struct Step {
     int count;
     size_t smem;
     lrb_plan* g;
-    bool panel = false;   // QR: the panel is staged in shared memory
     int threads = 0;      // SVD: threads per CTA
 };
 
-// Dynamic shared memory a QR CTA may take beyond its static arrays.
-size_t dyn_smem_limit(int device) {
-    int optin = 0;
-    cudaFuncAttributes fa;
-    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
-        cudaFuncGetAttributes(&fa, k_house_qr<true>) != cudaSuccess)
-        return 0;
-    return (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+// A QR step over `count` matrices of at most `rows` rows (the reflector in
+// shared memory).
+Step qr_step(size_t off, int count, int rows) {
+    return Step{Step::kQr, off, count, 8 * (size_t)rows + 16, nullptr};
 }
 
-// A QR step over `count` matrices of at most rows x cols: the shared-memory
-// panel form when rows x (cols + 1) doubles fit, else the in-place form.
-Step qr_step(size_t off, int count, int rows, int cols, size_t limit) {
-    const size_t panel = 8 * (size_t)rows * (cols + 1) + 16;
-    Step st{Step::kQr, off, count, 8 * (size_t)rows + 16, nullptr, false};
-    if (panel <= limit) {
-        st.smem = panel;
-        st.panel = true;
-    }
-    return st;
-}
-
-lrb_status set_smem_limits(size_t limit, size_t svd_smem_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(k_house_qr<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_house_qr<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(8 * LRB_LR_MAX_ROWS + 16));
+lrb_status set_smem_limits(size_t svd_smem_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(k_house_qr, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(8 * LRB_LR_MAX_ROWS + 16));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_jacobi_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)svd_smem_bytes);
     return e == cudaSuccess ? LRB_OK : cuda_err(e, "kernel shared-memory limit");
@@ -775,10 +748,7 @@ lrb_status finish(LrPlan* p, Uploader& up, const std::vector<Step>& steps) {
                 le = enqueue_fp64_plan(s.g, p->cap);
                 break;
             case Step::kQr:
-                if (s.panel)
-                    k_house_qr<true><<<s.count, kQrThreads, s.smem, p->cap>>>(at<QrDesc>(p->dmem, s.off));
-                else
-                    k_house_qr<false><<<s.count, kQrThreads, s.smem, p->cap>>>(at<QrDesc>(p->dmem, s.off));
+                k_house_qr<<<s.count, kQrThreads, s.smem, p->cap>>>(at<QrDesc>(p->dmem, s.off));
                 le = cudaGetLastError();
                 break;
             case Step::kSvd:
@@ -865,8 +835,7 @@ lrb_status create_rsvd(lrb_handle* h, const lrb_rsvd_desc* d, size_t count, int 
         destroy(p);
         return s;
     };
-    const size_t limit = dyn_smem_limit(p->device);
-    lrb_status s = set_smem_limits(limit, svd_smem(maxl));
+    lrb_status s = set_smem_limits(svd_smem(maxl));
     if (s != LRB_OK) return bail(s);
 
     Bump bump;
@@ -914,16 +883,16 @@ lrb_status create_rsvd(lrb_handle* h, const lrb_rsvd_desc* d, size_t count, int 
     const int c = (int)count;
     std::vector<Step> steps;
     steps.push_back({Step::kGemm, 0, 0, 0, pAO});
-    steps.push_back(qr_step(oY, c, maxm, maxl, limit));
+    steps.push_back(qr_step(oY, c, maxm));
     for (int it = 0; it < q; ++it) {
         steps.push_back({Step::kGemm, 0, 0, 0, pATY});
-        steps.push_back(qr_step(oZ, c, maxn, maxl, limit));
+        steps.push_back(qr_step(oZ, c, maxn));
         steps.push_back({Step::kGemm, 0, 0, 0, pAZ});
-        steps.push_back(qr_step(oY, c, maxm, maxl, limit));
+        steps.push_back(qr_step(oY, c, maxm));
     }
     steps.push_back({Step::kGemm, 0, 0, 0, pATY});
-    steps.push_back(qr_step(oZR, c, maxn, maxl, limit));
-    steps.push_back({Step::kSvd, oS, c, svd_smem(maxl), nullptr, false, jacobi_threads(maxl)});
+    steps.push_back(qr_step(oZR, c, maxn));
+    steps.push_back({Step::kSvd, oS, c, svd_smem(maxl), nullptr, jacobi_threads(maxl)});
     steps.push_back({Step::kGemm, 0, 0, 0, pU});
     steps.push_back({Step::kGemm, 0, 0, 0, pV});
     if ((s = finish(p, up, steps)) != LRB_OK) return bail(s);
@@ -1041,8 +1010,7 @@ lrb_status create_round_add(lrb_handle* h, const lrb_round_add_desc* d, size_t c
         destroy(p);
         return s;
     };
-    const size_t limit = dyn_smem_limit(p->device);
-    lrb_status s = set_smem_limits(limit, svd_smem(maxl));
+    lrb_status s = set_smem_limits(svd_smem(maxl));
     if (s != LRB_OK) return bail(s);
     Bump bump;
     struct Off {
@@ -1083,9 +1051,9 @@ lrb_status create_round_add(lrb_handle* h, const lrb_round_add_desc* d, size_t c
     const int c = (int)count;
     std::vector<Step> steps{{Step::kPack, oPU, c, 0, nullptr},
                             {Step::kPackT, oPV, c, 0, nullptr},
-                            qr_step(oQ1, c, maxm, maxl, limit),
-                            qr_step(oQ2, c, maxn, maxl, limit),
-                            {Step::kSvd, oS, c, svd_smem(maxl), nullptr, false, jacobi_threads(maxl)},
+                            qr_step(oQ1, c, maxm),
+                            qr_step(oQ2, c, maxn),
+                            {Step::kSvd, oS, c, svd_smem(maxl), nullptr, jacobi_threads(maxl)},
                             {Step::kGemm, 0, 0, 0, pU},
                             {Step::kGemm, 0, 0, 0, pV}};
     if ((s = finish(p, up, steps)) != LRB_OK) return bail(s);
