@@ -287,8 +287,10 @@ lrb_status lrb_queue_destroy(lrb_queue* q, int timeout_ms);
  * (host descriptor arrays, copied), runs on lrb_launch as a fixed sequence of
  * batched kernels (the FP64 GEMM path for every product, a Householder QR
  * kernel for the tall-skinny orthonormalisations, a one-sided Jacobi SVD
- * kernel for the small l x l cores), and reports its flops through
- * lrb_plan_get_info.  Outputs are WRITTEN and must not overlap any input or
+ * kernel, preconditioned by a pivoted QR, for the small l x l cores), and
+ * reports its flops through lrb_plan_get_info.  Singular values come out in
+ * descending order; a zero singular value gives a zero row of V (U's columns
+ * stay orthonormal).  Outputs are WRITTEN and must not overlap any input or
  * another output.  lrb_plan_status returns LRB_ERR_TIMEOUT when a Jacobi SVD
  * used its whole sweep limit without converging (its last iterate is
  * written).  Limits: l (and r1 + r2) <= LRB_LR_MAX_L, m, n <= LRB_LR_MAX_ROWS;

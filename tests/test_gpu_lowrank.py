@@ -208,6 +208,9 @@ def test_rsvd_zero_block(handle):
     (U, S, V), = rsvd_gpu(handle, [(A, rng.standard_normal((70, 12)), 5)], 1)[0]
     assert np.all(S == 0.0)
     assert np.all((U * S) @ V == 0.0)
+    # a zero singular value gives a zero row of V; U keeps orthonormal columns
+    assert np.all(V == 0.0)
+    assert np.abs(U.T @ U - np.eye(5)).max() <= 1e-15
 
 
 def test_rsvd_mixed_shapes_one_plan(handle):
