@@ -19,6 +19,14 @@ streams at once; step 3 waits for both.  Step 3 gives every block row one
 entry, so no two entries write the same part of Y.  Y's blocks interleave in
 memory (ld = N), so the byte-range alias check, which is conservative, is
 switched off for steps 1 and 3.
+
+The block rows are split into groups, each with its own three plans, so
+that step 3 of one group (a few long-k products that alone would leave a
+tail of idle SMs) overlaps step 2 of the next: the chains of all groups run
+in order on one stream, and each group has a stream of its own for step 1
+and, once that group's chains are done, step 3 (the long-k tiles of step 3
+are latency-bound, so the groups' steps 3 must overlap one another too).
+Groups write disjoint rows of Y and disjoint stacks T.
 """
 from __future__ import annotations
 
@@ -66,10 +74,11 @@ def random_blr(nb: int, b: int, r: int, seed: int = 0, device="cpu") -> BLRMatri
 class BLRMatVec:
     """Plans of Y += A X for a BLR matrix and fixed X / Y buffers (device,
     column-major N x nrhs with leading dimension N).  fused selects the fused
-    low-rank chain kernel (ranks <= 64) or the three-product comparator."""
+    low-rank chain kernel (ranks <= 64) or the three-product comparator;
+    groups is the number of block-row groups pipelined against each other."""
 
     def __init__(self, handle: L.Handle, M: BLRMatrix, X: torch.Tensor, Y: torch.Tensor, nrhs: int,
-                 fused: bool = True):
+                 fused: bool = True, groups: int = 2):
         nb, b, r, N = M.nb, M.b, M.r, M.N
         self.M, self.nrhs = M, nrhs
         dev = X.device
@@ -105,25 +114,40 @@ class BLRMatVec:
         d3["C"] = np.uint64(y0) + 8 * i * np.uint64(b)
         d3["m"], d3["n"], d3["k"], d3["lda"], d3["ldb"], d3["ldc"] = b, nrhs, (nb - 1) * r, b, (nb - 1) * r, N
         self.side = None
-        self.p1 = handle.plan(d1, check_alias=False, use_graph=True)
-        self.p2 = L.Plan(handle, d2, lr_fused=fused)
-        self.p3 = handle.plan(d3, check_alias=False, use_graph=True)
+        self.plans = []
+        for rows in np.array_split(np.arange(nb), max(1, min(groups, nb))):
+            i0, i1 = int(rows[0]), int(rows[-1]) + 1
+            q0, q1 = i0 * (nb - 1), i1 * (nb - 1)
+            self.plans.append((handle.plan(d1[i0:i1], check_alias=False, use_graph=True),
+                               L.Plan(handle, d2[q0:q1], lr_fused=fused),
+                               handle.plan(d3[i0:i1], check_alias=False, use_graph=True)))
 
     def run(self, stream=None):
         # steps 1 and 2 write different buffers (Y, T), so they run concurrently:
-        # the chains fill the SMs the diagonal product's last wave leaves idle
+        # the chains fill the SMs the diagonal products leave idle, and a
+        # group's step 3 overlaps the next groups' chains and steps 3
         s = stream if stream is not None else torch.cuda.current_stream()
         if self.side is None:
             self.side = torch.cuda.Stream(device=s.device)
-            self.ev_fork, self.ev_join = torch.cuda.Event(), torch.cuda.Event()
+            self.rows = [torch.cuda.Stream(device=s.device) for _ in self.plans]
+            self.ev_fork = torch.cuda.Event()
+            self.ev_chains = [torch.cuda.Event() for _ in self.plans]
+            self.ev_rows = [torch.cuda.Event() for _ in self.plans]
         self.ev_fork.record(s)
         self.side.wait_event(self.ev_fork)
-        self.p2.launch(self.side)
-        self.p1.launch(s)
-        self.ev_join.record(self.side)
-        s.wait_event(self.ev_join)
-        self.p3.launch(s)
+        for (_, p2, _), ev in zip(self.plans, self.ev_chains):
+            p2.launch(self.side)
+            ev.record(self.side)
+        for (p1, _, p3), rs, ev, done in zip(self.plans, self.rows, self.ev_chains, self.ev_rows):
+            rs.wait_event(self.ev_fork)
+            p1.launch(rs)
+            rs.wait_event(ev)
+            p3.launch(rs)
+            done.record(rs)
+        for done in self.ev_rows:
+            s.wait_event(done)
 
     def close(self):
-        for p in (self.p1, self.p2, self.p3):
-            p.close()
+        for group in self.plans:
+            for p in group:
+                p.close()

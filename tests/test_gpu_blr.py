@@ -1,7 +1,8 @@
 """BLR matrix times several right-hand sides (the paper's application,
 Sec. 7): Y += A X through the library (diagonal T-form batch, low-rank
 chains, one product per block row) against the oracle applied to the dense
-matrix assembled from the blocks.  Fused and unfused chains."""
+matrix assembled from the blocks.  Fused and unfused chains; block rows in
+one group, in uneven groups, and more groups asked for than block rows."""
 import numpy as np
 import pytest
 import torch
@@ -32,8 +33,8 @@ def dense(M):
     return A, mag
 
 
-@pytest.mark.parametrize("fused", [True, False])
-def test_blr_matvec_against_dense_oracle(fused):
+@pytest.mark.parametrize("fused,groups", [(True, 1), (True, 4), (False, 4), (True, 9)])
+def test_blr_matvec_against_dense_oracle(fused, groups):
     nb, b, r, nrhs = 6, 48, 4, 8
     M = blr.random_blr(nb, b, r, seed=3)
     N = nb * b
@@ -49,7 +50,7 @@ def test_blr_matvec_against_dense_oracle(fused):
     Xd = torch.tensor(X.ravel(order="F"), device="cuda")
     Yd = torch.tensor(Y0.ravel(order="F"), device="cuda")
     with L.Handle(0) as h:
-        mv = blr.BLRMatVec(h, Md, Xd, Yd, nrhs, fused=fused)
+        mv = blr.BLRMatVec(h, Md, Xd, Yd, nrhs, fused=fused, groups=groups)
         mv.run()
         torch.cuda.synchronize()
         mv.close()
