@@ -840,13 +840,13 @@ lrb_status create_rsvd(lrb_handle* h, const lrb_rsvd_desc* d, size_t count, int 
 
     Bump bump;
     struct Off {
-        size_t Y, Z, R, Ut, W, sig;
+        size_t Y, Z, R, Ut, W, sig, Vr;
     };
     std::vector<Off> off(count);
     for (size_t e = 0; e < count; ++e) {
-        const size_t m = d[e].out.m, n = d[e].out.n, l = d[e].l;
+        const size_t m = d[e].out.m, n = d[e].out.n, l = d[e].l, r = d[e].out.r;
         off[e] = Off{bump.take(m * l), bump.take(n * l), bump.take(l * l), bump.take(l * l), bump.take(l * l),
-                     bump.take(l)};
+                     bump.take(l), bump.take(n * r)};
     }
     s = alloc_work(p, bump.bytes);
     if (s != LRB_OK) return bail(s);
@@ -854,17 +854,19 @@ lrb_status create_rsvd(lrb_handle* h, const lrb_rsvd_desc* d, size_t count, int 
     std::vector<lrb_gemm_desc> gAO(count), gATY(count), gAZ(count), gU(count), gV(count);
     std::vector<QrDesc> qY(count), qZ(count), qZR(count);
     std::vector<SvdDesc> sv(count);
+    std::vector<PackDesc> pt(count);
     for (size_t e = 0; e < count; ++e) {
         const lrb_rsvd_desc& x = d[e];
         const lrb_lr_block& b = x.out;
         double *Y = wp(p, off[e].Y), *Z = wp(p, off[e].Z), *R = wp(p, off[e].R);
-        double *Ut = wp(p, off[e].Ut), *W = wp(p, off[e].W), *sig = wp(p, off[e].sig);
+        double *Ut = wp(p, off[e].Ut), *W = wp(p, off[e].W), *sig = wp(p, off[e].sig), *Vr = wp(p, off[e].Vr);
         const int m = b.m, n = b.n, l = x.l, r = b.r;
         gAO[e] = lrb_gemm_desc{x.A, x.Omega, Y, m, l, n, x.lda, x.ldo, m};          // Y = A Omega
         gATY[e] = lrb_gemm_desc{x.A, Y, Z, n, l, m, x.lda, m, n};                   // Z = A^T Q
         gAZ[e] = lrb_gemm_desc{x.A, Z, Y, m, l, n, x.lda, n, m};                    // Y = A Q~
         gU[e] = lrb_gemm_desc{Y, Ut, b.U, m, r, l, m, l, b.ldu};                    // U = Q U~_r
-        gV[e] = lrb_gemm_desc{W, Z, b.V, r, n, l, l, n, b.ldv};                     // V = W_r^T Q2^T
+        gV[e] = lrb_gemm_desc{Z, W, Vr, n, r, l, n, l, n};                          // V^T = Q2 W_r
+        pt[e] = PackDesc{Vr, nullptr, nullptr, nullptr, b.V, r, n, 0, n, 0, b.ldv};  // V = (V^T)^T
         qY[e] = QrDesc{Y, nullptr, m, l, m, 0};
         qZ[e] = QrDesc{Z, nullptr, n, l, n, 0};
         qZR[e] = QrDesc{Z, R, n, l, n, l};
@@ -873,13 +875,14 @@ lrb_status create_rsvd(lrb_handle* h, const lrb_rsvd_desc* d, size_t count, int 
     lrb_plan *pAO, *pATY, *pAZ = nullptr, *pU, *pV;
     if ((s = sub_plan(p, gAO, 0, 1, &pAO)) != LRB_OK || (s = sub_plan(p, gATY, 1, 1, &pATY)) != LRB_OK ||
         (q > 0 && (s = sub_plan(p, gAZ, 0, 1, &pAZ)) != LRB_OK) || (s = sub_plan(p, gU, 0, 1, &pU)) != LRB_OK ||
-        (s = sub_plan(p, gV, 3, 1, &pV)) != LRB_OK)
+        (s = sub_plan(p, gV, 0, 1, &pV)) != LRB_OK)
         return bail(s);
     Uploader up;
     const size_t oY = up.add(qY.data(), sizeof(QrDesc) * count);
     const size_t oZ = up.add(qZ.data(), sizeof(QrDesc) * count);
     const size_t oZR = up.add(qZR.data(), sizeof(QrDesc) * count);
     const size_t oS = up.add(sv.data(), sizeof(SvdDesc) * count);
+    const size_t oT = up.add(pt.data(), sizeof(PackDesc) * count);
     const int c = (int)count;
     std::vector<Step> steps;
     steps.push_back({Step::kGemm, 0, 0, 0, pAO});
@@ -895,6 +898,7 @@ lrb_status create_rsvd(lrb_handle* h, const lrb_rsvd_desc* d, size_t count, int 
     steps.push_back({Step::kSvd, oS, c, svd_smem(maxl), nullptr, jacobi_threads(maxl)});
     steps.push_back({Step::kGemm, 0, 0, 0, pU});
     steps.push_back({Step::kGemm, 0, 0, 0, pV});
+    steps.push_back({Step::kPackT, oT, c, 0, nullptr});
     if ((s = finish(p, up, steps)) != LRB_OK) return bail(s);
     std::memset(info, 0, sizeof(*info));
     info->entries = (int64_t)count;
@@ -1014,16 +1018,16 @@ lrb_status create_round_add(lrb_handle* h, const lrb_round_add_desc* d, size_t c
     if (s != LRB_OK) return bail(s);
     Bump bump;
     struct Off {
-        size_t Uc, Vt, R1, R2, Ut, W, sig;
+        size_t Uc, Vt, R1, R2, Ut, W, sig, Vr;
     };
     std::vector<Off> off(count);
     for (size_t e = 0; e < count; ++e) {
-        const size_t m = d[e].x.m, n = d[e].x.n, l = d[e].x.r + d[e].y.r;
+        const size_t m = d[e].x.m, n = d[e].x.n, l = d[e].x.r + d[e].y.r, r = d[e].out.r;
         off[e] = Off{bump.take(m * l), bump.take(n * l), bump.take(l * l), bump.take(l * l),
-                     bump.take(l * l), bump.take(l * l), bump.take(l)};
+                     bump.take(l * l), bump.take(l * l), bump.take(l),     bump.take(n * r)};
     }
     if ((s = alloc_work(p, bump.bytes)) != LRB_OK) return bail(s);
-    std::vector<PackDesc> pu(count), pv(count);
+    std::vector<PackDesc> pu(count), pv(count), pt(count);
     std::vector<QrDesc> q1(count), q2(count);
     std::vector<SvdDesc> sv(count);
     std::vector<lrb_gemm_desc> gU(count), gV(count);
@@ -1031,23 +1035,25 @@ lrb_status create_round_add(lrb_handle* h, const lrb_round_add_desc* d, size_t c
         const lrb_round_add_desc& x = d[e];
         const int m = x.x.m, n = x.x.n, l = x.x.r + x.y.r, r = x.out.r;
         double *Uc = wp(p, off[e].Uc), *Vt = wp(p, off[e].Vt), *R1 = wp(p, off[e].R1), *R2 = wp(p, off[e].R2);
-        double *Ut = wp(p, off[e].Ut), *W = wp(p, off[e].W), *sig = wp(p, off[e].sig);
+        double *Ut = wp(p, off[e].Ut), *W = wp(p, off[e].W), *sig = wp(p, off[e].sig), *Vr = wp(p, off[e].Vr);
         pu[e] = PackDesc{x.x.U, x.x.S, x.y.U, x.y.S, Uc, m, x.x.r, x.y.r, x.x.ldu, x.y.ldu, m};
         pv[e] = PackDesc{x.x.V, nullptr, x.y.V, nullptr, Vt, n, x.x.r, x.y.r, x.x.ldv, x.y.ldv, n};
         q1[e] = QrDesc{Uc, R1, m, l, m, l};
         q2[e] = QrDesc{Vt, R2, n, l, n, l};
         sv[e] = SvdDesc{R1, R2, Ut, W, sig, x.out.S, l, r};
         gU[e] = lrb_gemm_desc{Uc, Ut, x.out.U, m, r, l, m, l, x.out.ldu};
-        gV[e] = lrb_gemm_desc{W, Vt, x.out.V, r, n, l, l, n, x.out.ldv};
+        gV[e] = lrb_gemm_desc{Vt, W, Vr, n, r, l, n, l, n};                             // V^T = Q2 W_r
+        pt[e] = PackDesc{Vr, nullptr, nullptr, nullptr, x.out.V, r, n, 0, n, 0, x.out.ldv};  // V = (V^T)^T
     }
     lrb_plan *pU, *pV;
-    if ((s = sub_plan(p, gU, 0, 1, &pU)) != LRB_OK || (s = sub_plan(p, gV, 3, 1, &pV)) != LRB_OK) return bail(s);
+    if ((s = sub_plan(p, gU, 0, 1, &pU)) != LRB_OK || (s = sub_plan(p, gV, 0, 1, &pV)) != LRB_OK) return bail(s);
     Uploader up;
     const size_t oPU = up.add(pu.data(), sizeof(PackDesc) * count);
     const size_t oPV = up.add(pv.data(), sizeof(PackDesc) * count);
     const size_t oQ1 = up.add(q1.data(), sizeof(QrDesc) * count);
     const size_t oQ2 = up.add(q2.data(), sizeof(QrDesc) * count);
     const size_t oS = up.add(sv.data(), sizeof(SvdDesc) * count);
+    const size_t oT = up.add(pt.data(), sizeof(PackDesc) * count);
     const int c = (int)count;
     std::vector<Step> steps{{Step::kPack, oPU, c, 0, nullptr},
                             {Step::kPackT, oPV, c, 0, nullptr},
@@ -1055,7 +1061,8 @@ lrb_status create_round_add(lrb_handle* h, const lrb_round_add_desc* d, size_t c
                             qr_step(oQ2, c, maxn),
                             {Step::kSvd, oS, c, svd_smem(maxl), nullptr, jacobi_threads(maxl)},
                             {Step::kGemm, 0, 0, 0, pU},
-                            {Step::kGemm, 0, 0, 0, pV}};
+                            {Step::kGemm, 0, 0, 0, pV},
+                            {Step::kPackT, oT, c, 0, nullptr}};
     if ((s = finish(p, up, steps)) != LRB_OK) return bail(s);
     std::memset(info, 0, sizeof(*info));
     info->entries = (int64_t)count;
