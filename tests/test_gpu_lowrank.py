@@ -163,8 +163,10 @@ def check_factors(U, S, V, tol=1e-13):
     assert np.abs(V @ V.T - np.eye(r)).max() <= tol
 
 
+# (m, n, l, r); odd l (13, 27, 33, 1) exercises the SVD core's bye column and odd leading dimension
 CASES = [(200, 150, 20, 12), (64, 300, 26, 16), (333, 257, 40, 32), (97, 61, 8, 1), (96, 96, 96, 40),
-         (1024, 160, 42, 32), (50, 2000, 18, 8)]
+         (1024, 160, 42, 32), (50, 2000, 18, 8), (150, 120, 13, 5), (300, 200, 27, 16), (65, 70, 33, 20),
+         (40, 45, 1, 1)]
 
 
 @pytest.mark.parametrize("q", [0, 1, 2])
@@ -355,7 +357,8 @@ def round_add_gpu(handle, items):
 def test_round_add_known_spectrum(handle):
     rng = np.random.default_rng(31)
     items, want = [], []
-    for (m, n, r1, r2, r) in [(200, 150, 8, 8, 8), (96, 300, 16, 20, 24), (64, 64, 32, 32, 64), (50, 40, 3, 1, 2)]:
+    for (m, n, r1, r2, r) in [(200, 150, 8, 8, 8), (96, 300, 16, 20, 24), (64, 64, 32, 32, 64), (50, 40, 3, 1, 2),
+                              (150, 130, 5, 8, 7), (90, 80, 1, 2, 2)]:
         P, Q = orthonormal(rng, m, r1 + r2), orthonormal(rng, n, r1 + r2)
         s = rng.permutation(np.logspace(0, -3, r1 + r2))
         x = (P[:, :r1], s[:r1], Q[:, :r1].T.copy())
