@@ -980,6 +980,8 @@ lrb_status create_round_add(lrb_handle* h, const lrb_round_add_desc* d, size_t c
     *out = nullptr;
     if (!d) return fail0(LRB_ERR_INVALID, "host_descs is NULL");
     if (count == 0 || count > 0x7fffffffull) return failv(LRB_ERR_INVALID, "count %zu out of range", count);
+    if (count > 0x3fffffffull)   // one QR launch covers 2 x count matrices
+        return failv(LRB_ERR_UNSUPPORTED, "count %zu out of range", count);
     std::vector<Rng> rng;
     double flops = 0, bytes = 0;
     int maxl = 1, maxm = 1, maxn = 1;
@@ -1045,23 +1047,24 @@ lrb_status create_round_add(lrb_handle* h, const lrb_round_add_desc* d, size_t c
         gV[e] = lrb_gemm_desc{Vt, W, Vr, n, r, l, n, l, n};                             // V^T = Q2 W_r
         pt[e] = PackDesc{Vr, nullptr, nullptr, nullptr, x.out.V, r, n, 0, n, 0, x.out.ldv};  // V = (V^T)^T
     }
-    lrb_plan *pU, *pV;
-    if ((s = sub_plan(p, gU, 0, 1, &pU)) != LRB_OK || (s = sub_plan(p, gV, 0, 1, &pV)) != LRB_OK) return bail(s);
+    // The two QRs, and the products for U and V^T, are independent: one
+    // launch each over both halves, so neither ends on a half-empty wave.
+    q1.insert(q1.end(), q2.begin(), q2.end());
+    gU.insert(gU.end(), gV.begin(), gV.end());
+    lrb_plan* pUV;
+    if ((s = sub_plan(p, gU, 0, 1, &pUV)) != LRB_OK) return bail(s);
     Uploader up;
     const size_t oPU = up.add(pu.data(), sizeof(PackDesc) * count);
     const size_t oPV = up.add(pv.data(), sizeof(PackDesc) * count);
-    const size_t oQ1 = up.add(q1.data(), sizeof(QrDesc) * count);
-    const size_t oQ2 = up.add(q2.data(), sizeof(QrDesc) * count);
+    const size_t oQ = up.add(q1.data(), sizeof(QrDesc) * q1.size());
     const size_t oS = up.add(sv.data(), sizeof(SvdDesc) * count);
     const size_t oT = up.add(pt.data(), sizeof(PackDesc) * count);
     const int c = (int)count;
     std::vector<Step> steps{{Step::kPack, oPU, c, 0, nullptr},
                             {Step::kPackT, oPV, c, 0, nullptr},
-                            qr_step(oQ1, c, maxm),
-                            qr_step(oQ2, c, maxn),
+                            qr_step(oQ, 2 * c, std::max(maxm, maxn)),
                             {Step::kSvd, oS, c, svd_smem(maxl), nullptr, jacobi_threads(maxl)},
-                            {Step::kGemm, 0, 0, 0, pU},
-                            {Step::kGemm, 0, 0, 0, pV},
+                            {Step::kGemm, 0, 0, 0, pUV},
                             {Step::kPackT, oT, c, 0, nullptr}};
     if ((s = finish(p, up, steps)) != LRB_OK) return bail(s);
     std::memset(info, 0, sizeof(*info));
