@@ -147,10 +147,11 @@ __device__ __forceinline__ void reflect_column(const double* __restrict__ v, dou
 // Q = H_0 ... H_{cols-1} [I; 0] is formed in place, backwards.  A zero column
 // gives tau = 0 (H = I), so rank-deficient input still yields an orthonormal
 // Q.  The matrix is worked on in place in global memory (the panels of the
-// resident CTAs stay in L2), the current reflector in shared memory; two CTAs
-// per SM fill each other's barrier and scalar phases.  (Staging a whole panel
-// in shared memory leaves room for one CTA per SM and measured slower.)
-__global__ void __launch_bounds__(kQrThreads, 2) k_house_qr(const QrDesc* __restrict__ descs) {
+// resident CTAs stay in L2), the current reflector in shared memory; three
+// CTAs per SM (40 registers) fill each other's barrier and scalar phases.
+// (Staging a whole panel in shared memory leaves room for one CTA per SM and
+// measured slower.)
+__global__ void __launch_bounds__(kQrThreads, 3) k_house_qr(const QrDesc* __restrict__ descs) {
     extern __shared__ __align__(16) double sm[];
     __shared__ double red[kQrThreads + 1];
     __shared__ double s_tau[LRB_LR_MAX_L];
