@@ -392,6 +392,29 @@ def test_round_add_extremely_graded_spectrum(handle):
     assert np.linalg.norm((U * S) @ V - dense) <= 1e-13 * np.linalg.norm(dense)
 
 
+def test_round_add_benchmark_size_sampled(handle):
+    """512 rounded additions of 1024 x 1024 rank-16 blocks in one plan (the
+    benchmark's launch); y is 1e-5 below x, so the rank-16 truncation has a
+    gap and is well conditioned.  Pairs 0, 255 and 511 against the oracle."""
+    rng = np.random.default_rng(35)
+    m = n = 1024
+    r, cnt = 16, 512
+    items = []
+    for _ in range(cnt):
+        x = (rng.standard_normal((m, r)) / np.sqrt(m), np.logspace(0, -2, r), rng.standard_normal((r, n)) / np.sqrt(n))
+        y = (rng.standard_normal((m, r)) / np.sqrt(m), 1e-5 * np.logspace(0, -2, r),
+             rng.standard_normal((r, n)) / np.sqrt(n))
+        items.append((x, y, r))
+    outs = round_add_gpu(handle, items)
+    for e in (0, 255, 511):
+        (x, y, _), (U, S, V) = items[e], outs[e]
+        Uo, So, Vo = OL.lr_round_add(*x, *y, r)
+        dense = (x[0] * x[1]) @ x[2] + (y[0] * y[1]) @ y[2]
+        assert np.abs(S - So).max() <= 1e-12 * So[0], e
+        assert np.linalg.norm((U * S) @ V - (Uo * So) @ Vo) <= 1e-11 * np.linalg.norm(dense), e
+        check_factors(U, S, V)
+
+
 def test_round_add_random_matches_oracle(handle):
     rng = np.random.default_rng(32)
     items = []
