@@ -251,19 +251,23 @@ __device__ __forceinline__ void jacobi_pair(int round, int k, int L, int& p, int
 }
 
 // Lanes per column pair in k_jacobi_svd: the power of two T <= 32, with
-// pairs x T <= limit threads, that minimises a round's FP64 instructions on
-// the busiest SM sub-partition.  A warp instruction holds the FP64 pipe for
-// the same time whatever the number of active lanes, so a round costs each
+// pairs x T <= limit threads and at least two warps, that minimises the FP64
+// instructions of a round.  A warp instruction holds the FP64 pipe for the
+// same time whatever the number of active lanes, so a round costs each
 // working warp 11 ceil(l / T) instructions (3 dot-product FMAs and 8
 // rotation operations per row a lane owns), 3 log2 T (the butterfly sums)
-// and about 12 (the rotation angle), and warps w, w + 4, ... share one
-// sub-partition.
+// and about 12 (the rotation angle).  Batches put several cores on every SM,
+// so the total over the warps counts (one warp issuing back to back keeps a
+// sub-partition's FP64 pipe busy), not the busiest sub-partition; at least
+// two warps spread a core over two sub-partitions.  For l = 26..32 that is
+// T = 4, two warps per core (T = 8 with four took a rounded addition of 512
+// pairs, 32 x 32 cores, from 7.76 to 8.06 ms).
 __host__ __device__ inline int jacobi_lanes(int l, int limit) {
     const int np = ((l + 1) & ~1) / 2;
     int best = 1, best_cost = 0x7fffffff;
     for (int T = 1, lg = 0; T <= 32 && np * T <= limit; T *= 2, ++lg) {
         const int warps = (np * T + 31) / 32;
-        const int cost = ((warps + 3) / 4) * (11 * ((l + T - 1) / T) + 3 * lg + 12);
+        const int cost = warps < 2 ? 0x3fffffff : warps * (11 * ((l + T - 1) / T) + 3 * lg + 12);
         if (cost < best_cost) {
             best_cost = cost;
             best = T;
