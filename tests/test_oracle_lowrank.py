@@ -158,3 +158,22 @@ def test_round_add_exact_and_cancellation():
     assert fro_rel((U * S) @ V, dense) < 1e-13
     U, S, V = L.lr_round_add(U1, S1, V1, U1, -S1, V1, 3)
     assert np.abs(S).max() <= 1e-13 * np.linalg.norm((U1 * S1) @ V1, 2)
+
+
+def test_round_add_eckart_young_generic():
+    """Generic (non-orthogonal) factors: the rank-r result is the best rank-r
+    approximation of the dense sum (Eckart and Young), so its singular values
+    are the sum's r leading ones and its Frobenius error is the norm of the
+    rest -- both taken here from an SVD of the whole m x n sum, a route that
+    shares nothing with the oracle's QR of the stacked bases."""
+    rng = np.random.default_rng(33)
+    m, n, r1, r2 = 80, 55, 6, 9
+    U1, V1, S1 = rng.standard_normal((m, r1)), rng.standard_normal((r1, n)), np.logspace(0, -3, r1)
+    U2, V2, S2 = rng.standard_normal((m, r2)), rng.standard_normal((r2, n)), np.logspace(-1, -4, r2)
+    dense = (U1 * S1) @ V1 + (U2 * S2) @ V2
+    sig = np.linalg.svd(dense, compute_uv=False)
+    for r in (1, 5, 10, 15):
+        U, S, V = L.lr_round_add(U1, S1, V1, U2, S2, V2, r)
+        assert np.abs(S - sig[:r]).max() <= 1e-12 * sig[0]
+        err = np.linalg.norm(dense - (U * S) @ V)
+        assert abs(err - np.sqrt(np.sum(sig[r:] ** 2))) <= 1e-12 * sig[0]
