@@ -293,8 +293,9 @@ lrb_status lrb_queue_destroy(lrb_queue* q, int timeout_ms);
  * stay orthonormal).  Outputs are WRITTEN and must not overlap any input or
  * another output.  lrb_plan_status returns LRB_ERR_TIMEOUT when a Jacobi SVD
  * used its whole sweep limit without converging (its last iterate is
- * written).  Limits: l (and r1 + r2) <= LRB_LR_MAX_L, m, n <= LRB_LR_MAX_ROWS;
- * larger requests return LRB_ERR_UNSUPPORTED before any CUDA call. */
+ * written).  Limits: l (and r1 + r2) <= LRB_LR_MAX_L, m, n <= LRB_LR_MAX_ROWS,
+ * count < 2^30 for the rounded addition (one of its launches covers 2 x count
+ * matrices); larger requests return LRB_ERR_UNSUPPORTED before any CUDA call. */
 #define LRB_LR_MAX_L 96
 #define LRB_LR_MAX_ROWS 8192
 
