@@ -165,6 +165,8 @@ LOWRANK_MUTATIONS = {
     "expand_unscaled": ("return D + (U * S[None, :]) @ V", "return D + U @ V"),
     "round_add_unscaled": ("Uc = np.hstack([U1 * S1[None, :], U2 * S2[None, :]])", "Uc = np.hstack([U1, U2])"),
     "round_add_core_transposed": ("np.linalg.svd(R1 @ R2.T)", "np.linalg.svd(R2 @ R1.T)"),
+    "round_add_W_rows_for_columns": ("(Q2 @ Wt.T[:, :r]).T", "(Q2 @ Wt[:, :r]).T"),
+    "round_add_V_blocks_swapped": ("Vc = np.vstack([V1, V2])", "Vc = np.vstack([V2, V1])"),
 }
 
 
@@ -185,7 +187,8 @@ def lowrank_pins_pass(mod) -> bool:
     cases += [(T.test_range_finder_tail_bound, (q,)) for q in (0, 2)]
     cases += [(f, ()) for f in (T.test_eckart_young_full_sampling, T.test_power_iteration_sharpens,
                                 T.test_orthonormal_factors, T.test_expand_integer_and_identity,
-                                T.test_round_add_known_spectrum, T.test_round_add_exact_and_cancellation)]
+                                T.test_round_add_known_spectrum, T.test_round_add_exact_and_cancellation,
+                                T.test_round_add_eckart_young_generic)]
     saved = T.L
     T.L = mod
     try:
