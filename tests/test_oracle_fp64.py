@@ -9,7 +9,11 @@ other than the oracle itself:
   (C0 + P B), an integer rank-1 product, integer-valued random inputs;
 * Eq. 1's low-rank form U S V: (U S) V against U (S V) through the oracle,
   within twice the bound;
-* a library routine: numpy's matmul within the bound.
+* a library routine: numpy's matmul within the bound;
+* the bound helper |C0| + |A||B| (the element-wise tolerance of the GPU
+  comparisons): bitwise equal to the exact rational value on integer and
+  dyadic inputs with mixed signs and ld padding, within gamma_{2k+1} of it on
+  random inputs.
 """
 from fractions import Fraction
 
@@ -157,3 +161,58 @@ def test_batch_entry_points_agree(nthreads):
     I, J = I.ravel(), J.ravel()
     out = oracle.gemm_elements(A[I, :], B[:, J].T, c0.reshape(n, m).T[I, J])
     assert np.array_equal(out, full.reshape(n, m).T[I, J])
+
+
+def absbound_exact(m, n, k, A, B, C):
+    """|C0| + |A| |B| in exact rational arithmetic (Python fractions)."""
+    out = np.empty((m, n), dtype=object)
+    for i in range(m):
+        for j in range(n):
+            out[i, j] = abs(Fraction(C[i, j])) + sum(abs(Fraction(A[i, p])) * abs(Fraction(B[p, j]))
+                                                     for p in range(k))
+    return out
+
+
+def test_absbound_exact_on_integers_and_dyadic_rationals():
+    # oracle_gemm_absbound sets the element-wise tolerance of every FP64 GPU
+    # comparison, so it is pinned to |C0| + sum_p |a_ip| |b_pj| itself: on
+    # integer and small dyadic-rational inputs every product and partial sum
+    # is exact in binary64, so the helper must equal the exact value bitwise.
+    # Signs are mixed (an |.| left out changes the value), the padding rows
+    # hold huge values (reading them would show), and C0 is nonzero.
+    rng = np.random.default_rng(21)
+    for m, n, k, scale in [(1, 1, 1, 1.0), (5, 4, 3, 1.0), (17, 6, 33, 0.25), (9, 13, 70, 0.125)]:
+        pa, pb, pc = rng.integers(1, 4, 3)
+        A = np.full((m + pa, k), 1e300)
+        B = np.full((k + pb, n), -1e300)
+        C = np.full((m + pc, n), 1e300)
+        A[:m] = rng.integers(-8, 9, (m, k)) * scale
+        B[:k] = rng.integers(-8, 9, (k, n)) * scale
+        C[:m] = rng.integers(-1000, 1001, (m, n)) * scale
+        Af, Bf, Cf = (np.ascontiguousarray(X.ravel(order="F")) for X in (A, B, C))
+        got = oracle.absbound(m, n, k, Af, 0, m + pa, Bf, 0, k + pb, Cf, 0, m + pc)
+        exact = absbound_exact(m, n, k, A, B, C)
+        assert got.shape == (m, n)
+        for i in range(m):
+            for j in range(n):
+                assert Fraction(got[i, j]) == exact[i, j], (m, n, k, i, j)
+
+
+def test_absbound_random_within_one_rounding_per_term():
+    # Random binary64 inputs: the helper sums k + 1 nonnegative terms, so it is
+    # within gamma_{2k+1} (one rounding per product and per addition) of the
+    # exact value from below and above; offsets into a larger buffer are used.
+    rng = np.random.default_rng(22)
+    m, n, k = 7, 5, 40
+    A = rng.standard_normal((m, k)) * 10.0 ** rng.uniform(-3, 3, (m, k))
+    B = rng.standard_normal((k, n))
+    C = rng.standard_normal((m, n))
+    Af = np.concatenate([np.zeros(11), A.ravel(order="F")])
+    Bf = np.concatenate([np.zeros(5), B.ravel(order="F")])
+    Cf = np.concatenate([np.zeros(3), C.ravel(order="F")])
+    got = oracle.absbound(m, n, k, Af, 11, m, Bf, 5, k, Cf, 3, m)
+    exact = absbound_exact(m, n, k, A, B, C)
+    g = Fraction(oracle.gamma(2 * k + 1))
+    for i in range(m):
+        for j in range(n):
+            assert abs(Fraction(got[i, j]) - exact[i, j]) <= g * exact[i, j]

@@ -16,7 +16,10 @@ against something other than the oracle itself:
 * expansion: exact on integer data, identity factors;
 * rounded addition: two blocks built from disjoint columns of one
   orthonormal pair, so the singular values of the sum are known exactly; a
-  sum whose rank fits is reproduced; X + (-X) gives zero.
+  sum whose rank fits is reproduced; X + (-X) gives zero;
+* the flop count of the randomized SVD: its products against a count of the
+  multiply-adds the oracle really performs, its QRs and the whole count
+  against hand counts (Golub and Van Loan's Householder figures).
 """
 import numpy as np
 import pytest
@@ -177,3 +180,53 @@ def test_round_add_eckart_young_generic():
         assert np.abs(S - sig[:r]).max() <= 1e-12 * sig[0]
         err = np.linalg.norm(dense - (U * S) @ V)
         assert abs(err - np.sqrt(np.sum(sig[r:] ** 2))) <= 1e-12 * sig[0]
+
+
+class _CountingArray(np.ndarray):
+    """ndarray that adds 2 m k n to a counter for every m x k by k x n
+    matrix product taken with it (numpy's matmul ufunc), so the products the
+    oracle's randomized SVD actually performs can be counted."""
+    flops = 0
+
+    def __array_ufunc__(self, ufunc, method, *inputs, **kw):
+        raw = [np.asarray(x) if isinstance(x, _CountingArray) else x for x in inputs]
+        if ufunc is np.matmul and method == "__call__":
+            a, b = raw
+            _CountingArray.flops += 2 * a.shape[0] * a.shape[1] * b.shape[-1]
+        out = getattr(ufunc, method)(*raw, **kw)
+        return out.view(_CountingArray) if isinstance(out, np.ndarray) else out
+
+
+@pytest.mark.parametrize("m,n,l,r,q", [(30, 20, 6, 3, 0), (30, 20, 6, 3, 1), (41, 57, 9, 4, 2)])
+def test_lowrank_flops_against_counted_products(m, n, l, r, q):
+    # lowrank_flops is the throughput count of the randomized SVD.  Its product
+    # part is pinned by counting the multiply-adds of the products the oracle
+    # really takes (A Omega, q times A^T Q and A Q~, stage B's Q^T A, and
+    # U = Q U~_r); the GPU also forms V by one n x l by l x r product.  The
+    # QRs are counted by hand from Golub and Van Loan: Householder QR of a
+    # rows x l panel is 2 l^2 (rows - l/3) flops and forming its thin Q as
+    # much again; 1 + q panels of m rows and 1 + q of n rows.
+    rng = np.random.default_rng(m + n + q)
+    _CountingArray.flops = 0
+    A = rng.standard_normal((m, n)).view(_CountingArray)
+    Om = rng.standard_normal((n, l)).view(_CountingArray)
+    L.rsvd(A, Om, r, q)
+    counted = _CountingArray.flops
+    assert counted == 2 * m * n * l * (2 + 2 * q) + 2 * m * l * r
+    qr_hand = (1 + q) * 2 * (2 * l * l * (m - l / 3)) + (1 + q) * 2 * (2 * l * l * (n - l / 3))
+    assert L.lowrank_flops(m, n, l, r, q) == pytest.approx(counted + 2 * n * l * r + qr_hand, rel=1e-15)
+
+
+def test_lowrank_flops_literal_hand_count():
+    # m = n = 10, l = 4, r = 2, q = 1, by hand:
+    #   products with A: Y = A Omega, A^T Q, A Q~, A^T Q  -> 4 x 2 x 10 x 10 x 4 = 3200
+    #   QRs: 4 panels of 10 x 4, each 2 (2 * 16 * (10 - 4/3)) = 2 x 277.33.. = 554.66..
+    #        -> 2218.66.. (exactly 6656/3)
+    #   final products U (10 x 4 by 4 x 2) and V (10 x 4 by 4 x 2): 160 + 160 = 320
+    #   total 3200 + 6656/3 + 320 = 17216/3
+    assert L.lowrank_flops(10, 10, 4, 2, 1) == pytest.approx(17216 / 3, rel=1e-15)
+    # m = 1024, n = 1024, l = 26, r = 16, q = 1 (the benchmark's blocks):
+    #   4 x 2 x 1024^2 x 26 = 218103808; QRs: 4 panels of 1024 x 26, each
+    #   2 x 2 x 676 x (1024 - 26/3), together 10816 x 3046/3 = 32945536/3;
+    #   final 2 x 2 x 1024 x 26 x 16 = 1703936
+    assert L.lowrank_flops(1024, 1024, 26, 16, 1) == pytest.approx(218103808 + 32945536 / 3 + 1703936, rel=1e-15)

@@ -4,7 +4,17 @@ temporary copy of the oracle (on the CPU), makes at least one pin fail.
 C oracle: a flipped sign, a dropped last term, a transposed B index, the
 wrong leading dimension for A or C.  Split oracle: floor instead of
 round-to-nearest, an off-by-one exponent, a dropped digit level, digits
-combined with the wrong weight."""
+combined with the wrong weight.  Low-rank oracle: see LOWRANK_MUTATIONS.
+
+The bound helpers that set the GPU tolerances are covered the same way:
+|C0| + |A||B| (oracle_gemm_absbound) without |C0|, without an |.| on C0, A
+or B, or with C0 read at the wrong leading dimension; the split
+recombination magnitude without |C|, with signed terms, unscaled terms or
+the wrong level weight; the a-priori bound made looser (A's or B's rounding
+term doubled, the dropped pairs counted twice) or too small (a term left
+out); and the randomized SVD's flop count with the power iterations counted
+once, the QRs without forming Q, the final V product or the n-row panels
+miscounted."""
 import ctypes
 import importlib.util
 import os
@@ -210,3 +220,124 @@ def test_unmutated_lowrank_oracle_passes():
 @pytest.mark.parametrize("name", sorted(LOWRANK_MUTATIONS))
 def test_lowrank_mutation_is_caught(name):
     assert not lowrank_pins_pass(load_lowrank_mutant(*LOWRANK_MUTATIONS[name]))
+
+
+# The bound helpers that set the GPU tolerances: |C0| + |A||B| (C oracle),
+# the recombination magnitude and the a-priori bound (split oracle) and the
+# randomized SVD's flop count.  Each planted mistake -- an |.| or a term left
+# out, a scale or a weight wrong, a bound made looser -- fails a pin.
+ABSBOUND_MUTATIONS = {
+    "no_C0": ("= fabs(C0[(size_t)i", "= 0.0 * fabs(C0[(size_t)i"),
+    "signed_C0": ("= fabs(C0[(size_t)i + (size_t)j * (size_t)ldc]);", "= (C0[(size_t)i + (size_t)j * (size_t)ldc]);"),
+    "signed_A": ("+= fabs(A[(size_t)i + (size_t)p * (size_t)lda]) * b;", "+= A[(size_t)i + (size_t)p * (size_t)lda] * b;"),
+    "signed_B": ("double b = fabs(B[(size_t)p", "double b = (B[(size_t)p"),
+    "C0_wrong_ld": ("fabs(C0[(size_t)i + (size_t)j * (size_t)ldc])", "fabs(C0[(size_t)i + (size_t)j * (size_t)m])"),
+}
+
+
+def absbound_pins_pass(L) -> bool:
+    import test_oracle_fp64 as T
+    saved = oracle._lib
+    oracle._lib = L
+    try:
+        T.test_absbound_exact_on_integers_and_dyadic_rationals()
+        T.test_absbound_random_within_one_rounding_per_term()
+    except AssertionError:
+        return False
+    finally:
+        oracle._lib = saved
+    return True
+
+
+def test_unmutated_absbound_passes():
+    assert absbound_pins_pass(oracle.lib())
+
+
+@pytest.mark.parametrize("name", sorted(ABSBOUND_MUTATIONS))
+def test_absbound_mutation_is_caught(tmp_path, name):
+    L = build_mutant(tmp_path, *ABSBOUND_MUTATIONS[name])
+    dp = ctypes.POINTER(ctypes.c_double)
+    i32 = ctypes.c_int32
+    L.oracle_gemm_absbound.argtypes = [i32, i32, i32, dp, i32, dp, i32, dp, i32, dp]
+    L.oracle_gemm_absbound.restype = None
+    assert not absbound_pins_pass(L)
+
+
+SPLIT_HELPER_MUTATIONS = {
+    "recomb_no_C": ("    mag = np.abs(np.asarray(C, dtype=np.float64)).copy()\n    nchunks",
+                    "    mag = 0.0 * np.abs(np.asarray(C, dtype=np.float64))\n    nchunks"),
+    "recomb_signed_terms": ("mag += np.ldexp(np.abs(P).astype(np.float64)", "mag += np.ldexp(P.astype(np.float64)"),
+    "recomb_unscaled": ("mag += np.ldexp(np.abs(P).astype(np.float64), (E[:, None] + F[None, :] - p.beta * L).astype(np.int32))",
+                        "mag += np.abs(P).astype(np.float64)"),
+    "recomb_wrong_weight": ("- p.beta * L).astype(np.int32))\n    return mag", "- p.beta * (L - 1)).astype(np.int32))\n    return mag"),
+    "apriori_loose_rounding": ("ea = np.ldexp(1.0, (E - p.beta * p.S - 1).astype(np.int32))",
+                               "ea = np.ldexp(1.0, (E - p.beta * p.S).astype(np.int32))"),
+    "apriori_loose_B_rounding": ("* eb[None, :]\n        dropped", "* 2 * eb[None, :]\n        dropped"),
+    "apriori_dropped_twice": ("bound += (hi - lo) * dropped * sig", "bound += 2 * (hi - lo) * dropped * sig"),
+    "apriori_without_A_rounding": ("        bound += ea[:, None] * absB.sum(axis=0)[None, :]\n", ""),
+    "apriori_without_dropped": ("        if dropped:\n", "        if False:\n"),
+}
+
+
+def split_helper_pins_pass(S) -> bool:
+    import test_oracle_split as T
+    names = ("split_gemm", "apriori_bound", "recombination_magnitude", "split_digits", "chunk_exponents",
+             "chunk_level_sums")
+    saved = {n: getattr(oracle, n) for n in names}
+    for n in names:
+        setattr(oracle, n, getattr(S, n))
+    try:
+        for preset in ("bf16_s3", "fp16_s4"):
+            T.test_recombination_magnitude_exact(preset)
+            T.test_recombination_magnitude_wide_range(preset)
+            T.test_apriori_bound_is_attained(preset)
+            T.test_error_within_apriori_bound(preset)
+    except AssertionError:
+        return False
+    finally:
+        for n, f in saved.items():
+            setattr(oracle, n, f)
+    return True
+
+
+def test_unmutated_split_helpers_pass():
+    import oracle.split as S
+    assert split_helper_pins_pass(S)
+
+
+@pytest.mark.parametrize("name", sorted(SPLIT_HELPER_MUTATIONS))
+def test_split_helper_mutation_is_caught(name):
+    assert not split_helper_pins_pass(load_split_mutant(*SPLIT_HELPER_MUTATIONS[name]))
+
+
+FLOPS_MUTATIONS = {
+    "power_iteration_counted_once": ("gemm_a = 2.0 * m * n * l * (2 + 2 * q)", "gemm_a = 2.0 * m * n * l * (2 + q)"),
+    "qr_without_forming_Q": ("qr = lambda rows: 2.0 * (2.0 * rows", "qr = lambda rows: 1.0 * (2.0 * rows"),
+    "final_without_V": ("final = 2.0 * m * l * r + 2.0 * n * l * r", "final = 2.0 * m * l * r"),
+    "n_panels_as_m": ("qrs = (1 + q) * qr(m) + (1 + q) * qr(n)", "qrs = (1 + q) * qr(m) + (1 + q) * qr(m)"),
+}
+
+
+def flops_pins_pass(mod) -> bool:
+    import test_oracle_lowrank as T
+    saved = T.L
+    T.L = mod
+    try:
+        for args in [(30, 20, 6, 3, 0), (30, 20, 6, 3, 1), (41, 57, 9, 4, 2)]:
+            T.test_lowrank_flops_against_counted_products(*args)
+        T.test_lowrank_flops_literal_hand_count()
+    except AssertionError:
+        return False
+    finally:
+        T.L = saved
+    return True
+
+
+def test_unmutated_flops_pass():
+    from oracle import lowrank
+    assert flops_pins_pass(lowrank)
+
+
+@pytest.mark.parametrize("name", sorted(FLOPS_MUTATIONS))
+def test_flops_mutation_is_caught(name):
+    assert not flops_pins_pass(load_lowrank_mutant(*FLOPS_MUTATIONS[name]))
