@@ -1,34 +1,44 @@
 #!/usr/bin/env python3
 """Benchmark of the batched FP64 GEMM library (C_i += A_i B_i) on GB300.
 
-Workload (one "step"): the uniform-shape sweep -- b in {256, 512, 1024}
-(batch 4096 / 1024 / 256) x r in {16, 32, 64} x both forms (T-form
-C(b x r) += A(b x b) B(b x r), O-form C(b x b) += A(b x r) B(r x b)),
-N(0, 1) entries, 32,256 entries and 3.6e11 flops -- planned once and run as
-ONE persistent, graph-captured launch per step.  Inputs (~42 GB) exceed L2,
-so no flush is needed between steps.
+Workload of one step (the headline): the variable-size batch -- 20,000
+entries, b = round(exp(U(ln 64, ln 2048))), r uniform over {8, 16, 32, 64,
+128}, T-form C(b x r) += A(b x b) B(b x r) or O-form C(b x b) += A(b x r)
+B(r x b) with probability 1/2 each, N(0, 1), seed 3; A and B are views into a
+shared 4 GB operand pool and every entry has its own C (about 50 GB) --
+planned once with autotuned tiles and run as ONE persistent, graph-captured
+launch per step (1.18e12 flops).  The inputs exceed L2 many times over, so no
+flush is needed between steps.
 
-Reported beside it: the same plan through the one-launch-per-shape path
-(the comparator), the roofline of the persistent kernel against the FP64
-pipe, the end-to-end rate through the host-buffer C ABI call (copies in
-the timed region), SM clocks sampled during the timed region, and the CPU
-oracle timed on a bounded sample on the host cores.
+Beside it on the final JSON line: the same plan through one launch per
+distinct shape (the plain comparator), the roofline against the FP64 pipe's
+peak measured in the same run by a probe kernel, the end-to-end rate through
+the host-buffer call lrb_execute_host (copies in the timed region, with a
+breakdown of where its time goes), SM clocks sampled during the timed region,
+the CPU oracle timed on a bounded sample of the same batch, and short
+summaries of the split-precision error table and of the serving latencies.
+The other workloads' full results are printed on the line before it,
+prefixed "extras: ".
 
-`--impl reference` times the CPU oracle alone (the reference arm).
-Multi-GPU: every rank runs the full workload on its own GPU (weak scaling,
-entries are independent; no data-path collective), value = all ranks' flops
-over the slowest rank's time.
+`--impl reference` times the CPU oracle alone on a bounded sample of the same
+batch (the reference arm).  Multi-GPU (torchrun): `--scaling weak` (default)
+runs the whole batch on every rank's GPU; `--scaling strong` splits the
+batch's entries across the ranks by longest-processing-time order over their
+flops (lrb_partition_lpt), each rank planning and launching only its share.
+Entries are independent, so neither needs a data-path collective; value = all
+ranks' flops over the slowest rank's time.
 """
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 import numpy as np
@@ -38,14 +48,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "batched GEMM GFLOP/s and % roofline vs plain FP64 launch; serving p50/p99 ms"
 UNIT = "GFLOP/s"
-WORKLOAD = ("uniform-shape FP64 sweep: b in {256,512,1024} (batch 4096/1024/256) x r in {16,32,64} x "
-            "T-form (b x b)(b x r) and O-form (b x r)(r x b), N(0,1), one persistent graph launch per step")
+VARIABLE_COUNT = 20000
+WORKLOAD = ("variable-size FP64 batch: 20,000 entries, b log-uniform [64,2048], r in {8,16,32,64,128}, "
+            "T/O 50/50, N(0,1), seed 3, A/B views into a 4 GB pool; one persistent graph launch, autotuned tiles")
 DFMA_LANES_PER_SM_CLK = 2          # FP64 FMA lanes per SM per clock on GB300 (1.25 TFLOP/s nominal)
-# DRAM bytes per algorithmic byte of k_persistent, from the ncu capture in
-# profiles/k_persistent_fp64_uniform_sweep.md (small case of the same sweep),
-# valid while fp64_tiles.cu has the SHA-256 prefix below.
-TRAFFIC_PER_ALG_BYTE = 2.067912e9 / 2.018344960e9
-TRAFFIC_SOURCE_SHA = "c86a6ad4ee65ca25"
+# DRAM bytes (read + write) per algorithmic byte of k_persistent on the
+# variable-size batch, from an ncu capture of a 1/20-scale case of the same
+# batch (same 4 GB pool), valid while fp64_tiles.cu has the SHA-256 prefix
+# below; None until captured.
+TRAFFIC_PER_ALG_BYTE = None
+TRAFFIC_SOURCE_SHA = None
 
 
 def dist_env():
@@ -101,9 +113,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
-def fp64_peak_tflops(props, sm_max_mhz) -> float:
-    """FP64 pipe peak from unit counts and clock: SMs x 2 DFMA lanes x 2 flops x max SM clock."""
-    return props.multi_processor_count * DFMA_LANES_PER_SM_CLK * 2 * sm_max_mhz * 1e6 / 1e12
+def derived_fp64_peak_tflops(sms, mhz) -> float:
+    """FP64 pipe peak from unit counts and a clock: SMs x 2 DFMA lanes x 2 flops x clock."""
+    return sms * DFMA_LANES_PER_SM_CLK * 2 * mhz * 1e6 / 1e12
 
 
 def kernel_sha() -> str:
@@ -112,45 +124,162 @@ def kernel_sha() -> str:
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
 
 
+def fp64_probe(L, dev_index: int, seconds: float = 2.0) -> dict:
+    """The FP64 pipe's throughput measured by lrb_fp64_peak_probe (a DFMA
+    kernel over the whole GPU) for about `seconds`, with the SM clock sampled
+    while it runs."""
+    t_short, ms_short = L.lrb_fp64_peak_probe(dev_index, 1 << 14)
+    iters = max(1 << 14, int((1 << 14) * seconds * 1e3 / max(ms_short, 1e-3)))
+    s = ClockSampler(dev_index)
+    s.start()
+    tflops, ms = L.lrb_fp64_peak_probe(dev_index, iters)
+    clk = s.stop()
+    return {"tflops": tflops, "ms": ms, "iters": iters, "clocks": clk}
+
+
+# ---- host topology (where pinned host buffers live relative to the GPU) ----
+
+def _cpu_node(cpu: int):
+    d = f"/sys/devices/system/cpu/cpu{cpu}"
+    try:
+        for name in os.listdir(d):
+            if name.startswith("node") and name[4:].isdigit():
+                return int(name[4:])
+    except OSError:
+        pass
+    return None
+
+
+def gpu_numa_node(props):
+    for dom_fmt in ("{:04x}", "{:08x}"):
+        try:
+            bdf = (dom_fmt.format(props.pci_domain_id) + f":{props.pci_bus_id:02x}:{props.pci_device_id:02x}.0")
+            with open(f"/sys/bus/pci/devices/{bdf}/numa_node") as f:
+                return int(f.read().strip())
+        except (OSError, ValueError, AttributeError):
+            continue
+    return None
+
+
+def page_nodes(ptr: int, nbytes: int, samples: int = 64) -> dict:
+    """NUMA nodes of `samples` pages spread over [ptr, ptr + nbytes), from the
+    move_pages system call in query mode (nodes = NULL); {} where unsupported."""
+    nr = {"aarch64": 239, "x86_64": 279}.get(platform.machine())
+    if nr is None or nbytes <= 0:
+        return {}
+    page = os.sysconf("SC_PAGE_SIZE")
+    addrs = [(ptr + (nbytes - 1) * i // max(1, samples - 1)) & ~(page - 1) for i in range(samples)]
+    pages = (ctypes.c_void_p * samples)(*addrs)
+    status = (ctypes.c_int * samples)()
+    libc = ctypes.CDLL(None, use_errno=True)
+    libc.syscall.restype = ctypes.c_long
+    r = libc.syscall(ctypes.c_long(nr), ctypes.c_int(0), ctypes.c_ulong(samples), pages, None, status, ctypes.c_int(0))
+    if r != 0:
+        return {"error": os.strerror(ctypes.get_errno())}
+    hist = {}
+    for v in status:
+        hist[str(v)] = hist.get(str(v), 0) + 1
+    return hist
+
+
+def host_topology(props) -> dict:
+    cpus = sorted(os.sched_getaffinity(0))
+    nodes = {}
+    for c in cpus:
+        n = _cpu_node(c)
+        nodes[str(n)] = nodes.get(str(n), 0) + 1
+    return {"allowed_cpus": len(cpus), "cpu_nodes": nodes, "gpu_numa_node": gpu_numa_node(props),
+            "host_mem_gb": round(os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES") / 1e9, 1)}
+
+
+# ---- workloads -------------------------------------------------------------
+
+def variable_workload(device, count=VARIABLE_COUNT, rank=0, world=1, strong=False):
+    """The variable-size batch (all of it, or this rank's LPT share)."""
+    from paper_2311_07602_gb300 import workloads as W
+    forms, bs, rs = W.variable_shapes(VARIABLE_COUNT, seed=3)
+    if count != VARIABLE_COUNT:
+        forms, bs, rs = forms[:count], bs[:count], rs[:count]
+    if strong and world > 1:
+        from paper_2311_07602_gb300 import shard
+        m = bs.astype(np.int64)
+        n = np.where(forms == W.FORM_T, rs, bs).astype(np.int64)
+        k = np.where(forms == W.FORM_T, bs, rs).astype(np.int64)
+        part = shard.lpt_partition(m, n, k, world)
+        sel = np.nonzero(part == rank)[0]
+        forms, bs, rs = forms[sel], bs[sel], rs[sel]
+    return W.variable_batch(forms, bs, rs, seed=3, device=device, pool_elems=(4 << 30) // 8)
+
+
 def sweep_batches(device, scale=1.0):
     from paper_2311_07602_gb300 import workloads as W
     return [W.uniform_batch(f, b, r, max(1, int(round(n * scale))), dist="normal", seed=s, device=device)
             for f, b, r, n, s in W.uniform_sweep_groups()]
 
 
-def cpu_baseline(fraction: float, nthreads: int = 0):
-    """The oracle, as it stands, on the first `fraction` of every group of the
-    sweep (same shapes, seeds and distribution), timed on the host cores."""
-    import oracle
+def variable_sample_cpu(target_flops: float, seed: int = 33):
+    """A seeded random sample of the variable-size batch's entries (same
+    shapes, same value distribution) whose flops reach `target_flops`, on the
+    host (its operand pool is just large enough for the largest operand x 4)."""
     from paper_2311_07602_gb300 import workloads as W
-    total_flops, total_s, used = 0.0, 0.0, 1
-    entries = 0
-    for f, b, r, n, s in W.uniform_sweep_groups():
-        cnt = max(1, int(round(n * fraction)))
-        bt = W.uniform_batch(f, b, r, cnt, dist="normal", seed=s, device="cpu")
-        A, B, C = bt.A.numpy(), bt.B.numpy(), bt.C.numpy()
-        ents = [dict(A=A, B=B, C=C, offA=int(bt.offA[e]), offB=int(bt.offB[e]), offC=int(bt.offC[e]),
-                     m=int(bt.m[e]), n=int(bt.n[e]), k=int(bt.k[e]), lda=int(bt.lda[e]), ldb=int(bt.ldb[e]),
-                     ldc=int(bt.ldc[e])) for e in range(cnt)]
-        t0 = time.perf_counter()
-        used = oracle.gemm_batch(ents, nthreads=nthreads)
-        total_s += time.perf_counter() - t0
-        total_flops += bt.flops()
-        entries += cnt
-    return total_flops, total_s, used, entries
+    forms, bs, rs = W.variable_shapes(VARIABLE_COUNT, seed=3)
+    m = bs.astype(np.float64)
+    n = np.where(forms == W.FORM_T, rs, bs).astype(np.float64)
+    k = np.where(forms == W.FORM_T, bs, rs).astype(np.float64)
+    f = 2.0 * m * n * k
+    order = np.random.default_rng(seed).permutation(VARIABLE_COUNT)
+    cnt = int(np.searchsorted(np.cumsum(f[order]), target_flops)) + 1
+    sel = np.sort(order[:min(cnt, VARIABLE_COUNT)])
+    total_flops = float(f.sum())
+    return W.variable_batch(forms[sel], bs[sel], rs[sel], seed=seed, device="cpu"), total_flops
 
 
-def cpu_baseline_extras():
+def oracle_run(batch, nthreads: int = 0):
+    """The oracle, as it stands, on a host batch: (flops, seconds, threads)."""
+    import oracle
+    A, B, C = batch.A.numpy(), batch.B.numpy(), batch.C.numpy()
+    ents = [dict(A=A, B=B, C=C, offA=int(batch.offA[e]), offB=int(batch.offB[e]), offC=int(batch.offC[e]),
+                 m=int(batch.m[e]), n=int(batch.n[e]), k=int(batch.k[e]), lda=int(batch.lda[e]),
+                 ldb=int(batch.ldb[e]), ldc=int(batch.ldc[e])) for e in range(len(batch))]
+    t0 = time.perf_counter()
+    used = oracle.gemm_batch(ents, nthreads=nthreads)
+    return batch.flops(), time.perf_counter() - t0, used
+
+
+def cpu_baseline_variable(target_flops: float = 4e11) -> dict:
+    """The oracle on a bounded random sample of the variable-size batch,
+    timed on the host cores; also the full batch's time extrapolated by flops."""
+    sample, total_flops = variable_sample_cpu(target_flops)
+    f, s, used = oracle_run(sample)
+    rate = f / s / 1e9
+    return {"value": round(rate, 3), "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": (f"{len(sample)} of the 20,000 entries drawn at random (seed 33), {f:.3g} flops, {s:.1f} s "
+                       f"on the host cores; the full batch ({total_flops:.3g} flops) extrapolates to "
+                       f"{total_flops / (rate * 1e9):.0f} s")}
+
+
+def cpu_baseline_extras() -> dict:
     """The oracle, as it stands, on small samples of the other workloads
-    (same shapes and distributions), timed on the host cores: the paper's
-    low-rank chain (2000 blocks, b 1024, r 16; the paper's flop count), the
-    randomized SVD (4 kernel-matrix blocks, 1024^2, r 16, l 26, q 1; the
-    library's flop count) and the split-precision product (4 T-form entries,
-    1024 x 64 x 1024, BF16 S = 3; FP64-equivalent flops)."""
+    (same shapes and distributions), timed on the host cores: the uniform
+    sweep (the first 1/32 of every group), the paper's low-rank chain (2000
+    blocks, b 1024, r 16; the paper's flop count), the randomized SVD (4
+    kernel-matrix blocks, 1024^2, r 16, l 26, q 1; the library's flop count)
+    and the split-precision product (4 T-form entries, 1024 x 64 x 1024,
+    BF16 S = 3; FP64-equivalent flops)."""
     import oracle
     from oracle import lowrank as OL
     from paper_2311_07602_gb300 import workloads as W
     out = {}
+    fl, secs, ents = 0.0, 0.0, 0
+    for f, b, r, n, s in W.uniform_sweep_groups():
+        cnt = max(1, n // 32)
+        bt = W.uniform_batch(f, b, r, cnt, dist="normal", seed=s, device="cpu")
+        ff, ss, used = oracle_run(bt)
+        fl += ff
+        secs += ss
+        ents += cnt
+    out["uniform_sweep"] = {"gflops": round(fl / secs / 1e9, 2), "threads": used,
+                            "sample": f"first 1/32 of every group ({ents} entries)"}
     lb = W.lr_batch(2000, 1024, 16, seed=7016, device="cpu")
     host = {k: t.numpy() for k, t in lb.bufs.items()}
     t0 = time.perf_counter()
@@ -181,28 +310,31 @@ def cpu_baseline_extras():
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle, as it stands, on a bounded random
+    sample of the variable-size batch per step (the same sample every step)."""
     rank, _, world = dist_env()
     if world > 1 and rank != 0:
         return 0
-    sys.path.insert(0, ROOT)
     from oracle import build as ob
     ob.build()
-    frac = args.ref_fraction
+    sample, total_flops = variable_sample_cpu(args.ref_flops)
     for _ in range(args.warmup):
-        cpu_baseline(frac / 4)
-    flops, secs = 0.0, 0.0
-    used, ents = 1, 0
+        oracle_run(sample)
+    flops, secs, used = 0.0, 0.0, 1
     for _ in range(args.steps):
-        f, s, used, ents = cpu_baseline(frac)
+        c0 = sample.C.clone()
+        f, s, used = oracle_run(sample)
+        sample.C.copy_(c0)
         flops += f
         secs += s
     val = flops / secs / 1e9
-    sample = f"first {frac:.4g} of every group of the sweep ({ents} entries, {flops / args.steps:.3g} flops) per step"
+    desc = (f"{len(sample)} of the 20,000 entries drawn at random (seed 33), {flops / args.steps:.3g} flops per step; "
+            f"the full batch ({total_flops:.3g} flops) extrapolates to {total_flops / (val * 1e9):.0f} s")
     line = {"impl": "reference", "metric": METRIC, "value": round(val, 3), "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * secs / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": sample},
-            "cpu_baseline": {"value": round(val, 3), "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
+            "config": {"workload": WORKLOAD, "sample": desc},
+            "cpu_baseline": {"value": round(val, 3), "unit": UNIT, "cores": used, "kind": "oracle", "sample": desc},
             "e2e": {"value": round(val, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -214,24 +346,29 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lrbatch", choices=["lrbatch", "reference"])
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="multi-GPU: every rank runs the whole batch (weak) or its LPT share of it (strong)")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--cpu-fraction", type=float, default=1.0)
-    ap.add_argument("--ref-fraction", type=float, default=1 / 32)
+    ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--ref-flops", type=float, default=3e10, help="oracle flops per reference-arm step")
+    ap.add_argument("--cpu-flops", type=float, default=4e11, help="oracle flops of the cpu_baseline sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--no-extras", action="store_true",
-                    help="skip the other workloads (64-entry O-form, variable-size, split precision, serving)")
-    ap.add_argument("--extras", default="small,variable,split,serving,dmma,lr,blr,lowrank",
-                    help="comma-separated subset of the other workloads to run")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other workloads")
+    ap.add_argument("--extras", default="sweep,small,split,serving,dmma,lr,blr,lowrank",
+                    help="comma-separated subset of the other workloads (also: sweep_e2e)")
     ap.add_argument("--split-batch", type=int, default=2048, help="entries of the split-precision batch")
     ap.add_argument("--dmma-scale", type=float, default=0.25, help="batch-count scale of the DMMA comparison")
     ap.add_argument("--lr-batch", type=int, default=20000, help="blocks per low-rank chain configuration")
     ap.add_argument("--lr-ranks", default="8,16,32,96,128", help="ranks of the low-rank chain sweep")
     ap.add_argument("--lowrank-count", type=int, default=1024,
                     help="dense blocks of the randomized-SVD / expansion / rounded-addition leg")
-    ap.add_argument("--scale", type=float, default=1.0,
-                    help="batch-count scale of every group (profiling runs use a small case)")
+    ap.add_argument("--serving-secs", type=float, default=60.0, help="seconds per 0.25-0.9x capacity point")
+    ap.add_argument("--overload-secs", type=float, default=10.0, help="seconds per stated overload rate")
+    ap.add_argument("--count", type=int, default=VARIABLE_COUNT,
+                    help="entries of the headline batch (profiling runs use a small case; the first N of the 20,000)")
+    ap.add_argument("--sweep-scale", type=float, default=1.0, help="batch-count scale of the uniform sweep extra")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -247,6 +384,7 @@ def main():
         pg = dist
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
+    strong = args.scaling == "strong" and world > 1
 
     def barrier():
         if pg is not None:
@@ -259,19 +397,19 @@ def main():
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         return float(t.item())
 
+    def sum_over_ranks(x: float) -> float:
+        if pg is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64)
+        pg.all_reduce(t)
+        return float(t.item())
+
     from paper_2311_07602_gb300 import lrbatch as L
-    batches = sweep_batches(dev, args.scale)
-    descs = np.concatenate([L.descs_for(b) for b in batches])
-    flops = float(sum(b.flops() for b in batches))
-    alg_bytes = float(sum(b.alg_bytes() for b in batches))
     cache = os.environ.get("LRB_TUNE_CACHE") or os.path.join(tempfile.gettempdir(), f"lrb_tune_{local_rank}.json")
     os.environ["LRB_TUNE_CACHE"] = cache
     handle = L.Handle(local_rank)
-    t0 = time.perf_counter()
-    plan = handle.plan(descs, use_graph=True)
-    plan_s = time.perf_counter() - t0
-    info = plan.info()
     stream = torch.cuda.Stream(device=dev)
+    props = torch.cuda.get_device_properties(dev)
 
     def timed(fn, steps, warmup):
         with torch.cuda.stream(stream):
@@ -294,70 +432,77 @@ def main():
         per = [e0.elapsed_time(e1) for e0, e1 in evs]
         return total_ms, per
 
+    # ---- the headline: the variable-size batch, one persistent graph launch per step
+    vb = variable_workload(dev, args.count, rank, world, strong)
+    descs = L.descs_for(vb)
+    flops = vb.flops()
+    alg_bytes = vb.alg_bytes()
+    t0 = time.perf_counter()
+    plan = handle.plan(descs, use_graph=True)
+    plan_s = time.perf_counter() - t0
+    info = plan.info()
+    probe = fp64_probe(L, local_rank)
+
     sampler = ClockSampler(local_rank)
     sampler.start()
     total_ms, per = timed(lambda s: plan.launch(s), args.steps, args.warmup)
     clocks = sampler.stop()
     total_ms = max_over_ranks(total_ms)
-    value = world * flops * args.steps / (total_ms / 1e3) / 1e9
+    all_flops = sum_over_ranks(flops) if strong else world * flops
+    value = all_flops * args.steps / (total_ms / 1e3) / 1e9
     ms_per_step = total_ms / args.steps
 
-    props = torch.cuda.get_device_properties(dev)
-    sm_max = clocks.get("sm_max_mhz") or 2070.0
-    peak = fp64_peak_tflops(props, sm_max)
+    run_mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    probe_mhz = probe["clocks"].get("sm_mhz") or run_mhz
+    peak = probe["tflops"] * run_mhz / probe_mhz
+    derived = derived_fp64_peak_tflops(props.multi_processor_count, clocks.get("sm_max_mhz") or 2070.0)
     achieved = flops / (statistics.mean(per) / 1e3) / 1e12
+    traffic = None
+    if TRAFFIC_PER_ALG_BYTE is not None and kernel_sha() == TRAFFIC_SOURCE_SHA:
+        traffic = round(TRAFFIC_PER_ALG_BYTE * alg_bytes)
     line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "scaling": "strong" if strong else "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded N(0,1), generated on the device)",
-            "config": {"workload": WORKLOAD if args.scale == 1.0 else f"{WORKLOAD} (batch counts x {args.scale})",
-                       "entries": int(info["entries"]), "tiles": int(info["items"]),
-                       "flops_per_step": flops, "alg_bytes_per_step": alg_bytes, "persistent_grid": int(info["grid"]),
+            "config": {"workload": WORKLOAD if args.count == VARIABLE_COUNT else
+                       f"{WORKLOAD} (first {args.count} entries)",
+                       "entries": int(info["entries"]), "tiles": int(info["items"]), "flops_per_step": flops,
+                       "alg_bytes_per_step": alg_bytes, "persistent_grid": int(info["grid"]),
                        "l2": "inputs larger than L2 (%.0f GB per step), no flush" % (alg_bytes / 1e9),
-                       "plan_s": round(plan_s, 3)},
+                       "plan_s_incl_tuning": round(plan_s, 2)},
             "gpu_launches": args.steps,
             "roofline": {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
-                         "frac": round(achieved / peak, 4),
-                         "traffic": (round(TRAFFIC_PER_ALG_BYTE * alg_bytes) if kernel_sha() == TRAFFIC_SOURCE_SHA
-                                     else None),
-                         "traffic_note": "DRAM bytes per launch, scaled by algorithmic bytes from the small-case ncu "
-                                         "capture (profiles/k_persistent_fp64_uniform_sweep.md); null if the kernel "
-                                         "source changed since",
+                         "frac": round(achieved / peak, 4), "traffic": traffic,
                          "kernel": "k_persistent (FP64 DFMA tiles)",
-                         "peak_source": "derived: SMs x 2 DFMA lanes/clk x 2 flop x max SM clock",
-                         "peak_measured_probe_tflops": 1.2029},
+                         "peak_source": "measured: lrb_fp64_peak_probe (DFMA kernel, whole GPU) in this run, "
+                                        "scaled by the median SM clock of the timed region over the probe's",
+                         "probe": {"tflops": round(probe["tflops"], 4), "sm_mhz": probe_mhz, "ms": round(probe["ms"], 1)},
+                         "derived_peak": round(derived, 4), "frac_of_derived": round(achieved / derived, 4)},
             "clocks": clocks}
-    line["pct_roofline"] = round(100 * achieved / peak, 2)
 
     if not args.no_plain:
-        p_ms, p_per = timed(lambda s: plan.launch_plain(s), args.steps, args.warmup)
+        p_ms, _ = timed(lambda s: plan.launch_plain(s), args.plain_steps, 1 + 2)
         p_ms = max_over_ranks(p_ms)
-        pval = world * flops * args.steps / (p_ms / 1e3) / 1e9
-        line["plain"] = {"value": round(pval, 2), "unit": UNIT, "ms_per_step": round(p_ms / args.steps, 3),
+        pval = all_flops * args.plain_steps / (p_ms / 1e3) / 1e9
+        line["plain"] = {"value": round(pval, 2), "unit": UNIT, "ms_per_step": round(p_ms / args.plain_steps, 3),
                          "launches_per_step": int(info["groups"])}
         line["vs_plain"] = round(value / pval, 4)
+    plan.close()
 
     if not args.no_e2e:
-        line["e2e"] = e2e_leg(L, handle, batches, flops, args, barrier, max_over_ranks, world, stream)
+        line["e2e"] = e2e_leg(L, [vb], args.e2e_steps, args.warmup, barrier, max_over_ranks, world, local_rank,
+                              props, strong, sum_over_ranks)
+    del vb
+    torch.cuda.empty_cache()
 
+    ex = {}
     if not args.no_extras and world == 1:
-        plan.close()
-        plan = None
-        del batches
-        torch.cuda.empty_cache()
-        line["extras"] = extras(L, handle, stream, dev, peak, timed, set(args.extras.split(",")), args.split_batch,
-                                args.dmma_scale, args.lr_batch, tuple(int(x) for x in args.lr_ranks.split(",")),
-                                args.lowrank_count)
+        ex = extras(L, handle, stream, dev, peak, timed, set(args.extras.split(",")), args, props)
+        print("extras: " + json.dumps(ex), flush=True)
+        line["north_star"] = north_star_summary(ex)
 
     if not args.no_cpu and rank == 0 and world == 1:
-        f, s, used, ents = cpu_baseline(args.cpu_fraction)
-        line["cpu_baseline"] = {"value": round(f / s / 1e9, 3), "unit": UNIT, "cores": used, "kind": "oracle",
-                                "sample": (f"first {args.cpu_fraction:.3g} of every group of the sweep "
-                                           f"({ents} entries, {f:.3g} flops, {s:.1f} s on the host cores)")}
-        if not args.no_extras:
-            line["cpu_baseline"]["extras"] = cpu_baseline_extras()
-    if plan is not None:
-        plan.close()
+        line["cpu_baseline"] = cpu_baseline_variable(args.cpu_flops)
     handle.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -366,39 +511,84 @@ def main():
     return 0
 
 
-def extras(L, handle, stream, dev, peak_fp64, timed, which, split_batch, dmma_scale=0.25, lr_batch=20000,
-           lr_ranks=(8, 16, 32, 96, 128), lowrank_count=1024):
-    """The other workloads, each with its own plan, 3 warm-up and 5 timed launches:
-    the 64-entry O-form batch (L2 flushed before every launch: it fits in L2),
-    the 20,000-entry variable-size batch (persistent vs one launch per shape),
-    and the split-precision batch (b 1024, r 64, 2048 entries, 10^U(-4,4) N(0,1))."""
+def north_star_summary(ex: dict) -> dict:
+    """The named targets in a few fields: the split-precision error per preset
+    and form (against the FP64 path) with its fraction of the HBM roof, and the
+    serving latencies with their sample counts."""
+    out = {}
+    sp = ex.get("split")
+    if sp:
+        out["split_rel_err_vs_fp64"] = {f: {k: v["rel_fro_err_vs_fp64"] for k, v in sp[f].items() if k != "fp64"}
+                                        for f in ("T", "O") if f in sp}
+        out["split_frac_hbm"] = {f: {k: v["frac_hbm"] for k, v in sp[f].items() if k != "fp64"}
+                                 for f in ("T", "O") if f in sp}
+    sv = ex.get("serving")
+    if sv:
+        out["serving_p50_p99_ms_n"] = [[p["load"], p["p50_ms"], p["p99_ms"], p["completed"]] for p in sv["points"]]
+        out["serving_capacity_req_s"] = sv["capacity_req_s"]
+    sw = ex.get("uniform_sweep")
+    if sw:
+        out["uniform_sweep_gflops"] = sw["gflops"]
+        out["uniform_sweep_frac"] = sw["frac_fp64_peak"]
+    out["alone_equals_mix"] = "bitwise, tests/test_gpu_serving.py (FP64 and split waves)"
+    return out
+
+
+def extras(L, handle, stream, dev, peak_fp64, timed, which, args, props):
+    """The other workloads, each with its own plan."""
     import torch
-    from paper_2311_07602_gb300 import workloads as W
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
-    out = {}
-
+    out = {"fp64_peak_tflops": round(peak_fp64, 4)}
+    if "sweep" in which:
+        out["uniform_sweep"] = sweep_leg(L, handle, dev, peak_fp64, timed, args.sweep_scale)
+    if "sweep_e2e" in which:
+        bts = sweep_batches(dev, args.sweep_scale)
+        out["uniform_sweep_e2e"] = e2e_leg(L, bts, args.e2e_steps, args.warmup, lambda: None, lambda x: x, 1,
+                                           dev.index or 0, props, False, lambda x: x)
+        del bts
+        torch.cuda.empty_cache()
     if "small" in which:
         out["small_o_form"] = small_leg(L, handle, stream, dev, peak_fp64)
-    if "variable" in which:
-        out["variable_size"] = variable_leg(L, handle, dev, peak_fp64, timed)
     if "split" in which:
-        out["split"] = split_leg(L, handle, dev, timed, hbm, split_batch)
+        out["split"] = split_leg(L, handle, dev, timed, hbm, args.split_batch)
     if "serving" in which:
-        out["serving"] = serving_leg(L, handle, dev, peak_fp64)
+        out["serving"] = serving_leg(L, handle, dev, peak_fp64, args.serving_secs, args.overload_secs)
     if "dmma" in which:
-        out["dmma"] = dmma_leg(L, handle, dev, peak_fp64, timed, dmma_scale)
+        out["dmma"] = dmma_leg(L, handle, dev, peak_fp64, timed, args.dmma_scale)
     if "lr" in which:
-        out["lr_chain"] = lr_leg(L, handle, dev, peak_fp64, timed, lr_batch, lr_ranks)
+        out["lr_chain"] = lr_leg(L, handle, dev, peak_fp64, timed, args.lr_batch,
+                                 tuple(int(x) for x in args.lr_ranks.split(",")))
     if "blr" in which:
         out["blr_matvec"] = blr_leg(L, handle, dev, peak_fp64, timed)
     if "lowrank" in which:
-        out["lowrank"] = lowrank_leg(L, handle, dev, peak_fp64, timed, count=lowrank_count)
+        out["lowrank"] = lowrank_leg(L, handle, dev, peak_fp64, timed, count=args.lowrank_count)
     return out
+
+
+def sweep_leg(L, handle, dev, peak_fp64, timed, scale=1.0):
+    """The uniform-shape sweep (b in {256, 512, 1024} x r in {16, 32, 64} x
+    both forms, 32,256 entries, N(0,1)) as one persistent graph launch, and
+    through one launch per shape."""
+    import torch
+    batches = sweep_batches(dev, scale)
+    descs = np.concatenate([L.descs_for(b) for b in batches])
+    f = float(sum(b.flops() for b in batches))
+    with handle.plan(descs, use_graph=True) as p:
+        info = p.info()
+        ms, _ = timed(lambda s: p.launch(s), 5, 3)
+        ms_q, _ = timed(lambda s: p.launch_plain(s), 3, 3)
+    del batches
+    torch.cuda.empty_cache()
+    return {"workload": "b in {256,512,1024} (batch 4096/1024/256) x r in {16,32,64} x T/O, N(0,1)"
+                        + ("" if scale == 1.0 else f" (batch counts x {scale})"),
+            "gflops": round(f * 5 / ms / 1e6, 1), "ms": round(ms / 5, 3),
+            "frac_fp64_peak": round(f * 5 / ms / 1e9 / peak_fp64, 4),
+            "plain_gflops": round(f * 3 / ms_q / 1e6, 1), "plain_launches": int(info["groups"])}
 
 
 def lowrank_leg(L, handle, dev, peak_fp64, timed, count=1024, b=1024, r=16, p=10, q=1):
@@ -604,78 +794,67 @@ def small_leg(L, handle, stream, dev, peak_fp64):
             "gflops": round(f / ms / 1e6, 2), "ms": round(ms, 4), "frac_fp64_peak": round(f / ms / 1e9 / peak_fp64, 4)}
 
 
-def variable_leg(L, handle, dev, peak_fp64, timed):
-    """20,000 entries, b log-uniform [64, 2048], r in {8..128}, T/O 50/50:
-    one persistent graph launch against one launch per distinct shape."""
-    import torch
-    from paper_2311_07602_gb300 import workloads as W
-    forms, bs, rs = W.variable_shapes(20000, seed=3)
-    vb = W.variable_batch(forms, bs, rs, seed=3, device=dev, pool_elems=(4 << 30) // 8)
-    t0 = time.perf_counter()
-    p = handle.plan(L.descs_for(vb), use_graph=True)
-    plan_s = time.perf_counter() - t0
-    info = p.info()
-    f = vb.flops()
-    ms_p, _ = timed(lambda s: p.launch(s), 5, 3)
-    ms_q, _ = timed(lambda s: p.launch_plain(s), 5, 3)
-    out = {
-        "workload": "20,000 entries, b log-uniform [64,2048], r in {8,16,32,64,128}, T/O 50/50, N(0,1), seed 3, "
-                    "A/B views into a 4 GB pool",
-        "flops": f, "persistent_gflops": round(f * 5 / ms_p / 1e6, 2), "plain_gflops": round(f * 5 / ms_q / 1e6, 2),
-        "vs_plain": round(ms_q / ms_p, 4), "frac_fp64_peak": round(f * 5 / ms_p / 1e9 / peak_fp64, 4),
-        "persistent_ms": round(ms_p / 5, 3), "plain_ms": round(ms_q / 5, 3), "plain_launches": int(info["groups"]),
-        "tiles": int(info["items"]), "plan_s_incl_tuning": round(plan_s, 2)}
-    p.close()
-    # the same variable-size batch in split precision (one persistent tcgen05 launch over all tiles)
-    for name, prec in (("split_bf16_s3", L.LRB_PREC_SPLIT_BF16_S3), ("split_bf16_s4", L.LRB_PREC_SPLIT_BF16_S4)):
-        with handle.plan(L.descs_for(vb), precision=prec) as ps:
-            ms_s, _ = timed(lambda s: ps.launch(s), 3, 3)
-            st = ps.status()
-        out[name] = {"gflops_fp64_equiv": round(f * 3 / ms_s / 1e6, 1), "ms": round(ms_s / 3, 3),
-                     "vs_fp64_persistent": round((ms_p / 5) / (ms_s / 3), 3), "status": int(st)}
-    del vb
-    torch.cuda.empty_cache()
-    return out
-
-
 def split_leg(L, handle, dev, timed, hbm, batch):
     """Split precision (BF16/FP16 x 3/4 digits) against the FP64 path on the
-    wide-range batch b 1024, r 64, entries 10^U(-4,4) N(0,1), both forms."""
+    wide-range batch b 1024, r 64, entries 10^U(-4,4) N(0,1), both forms.  The
+    error of each path is measured on one application to a zeroed C against
+    the FP64 (DFMA) path's product, whose own error against the oracle the
+    tests bound by 1e-13: relative Frobenius error over the whole batch and
+    the largest per-entry one.  FP64 DMMA tiles (forced) are measured too."""
     import torch
     from paper_2311_07602_gb300 import workloads as W
     res = {}
+    paths = (("fp64", dict(precision=L.LRB_PREC_FP64, use_graph=True)),
+             ("fp64_dmma", dict(precision=L.LRB_PREC_FP64_DMMA_ALLOWED, use_graph=True, force_variant=9)),
+             ("bf16_s3", dict(precision=L.LRB_PREC_SPLIT_BF16_S3)), ("bf16_s4", dict(precision=L.LRB_PREC_SPLIT_BF16_S4)),
+             ("fp16_s3", dict(precision=L.LRB_PREC_SPLIT_FP16_S3)), ("fp16_s4", dict(precision=L.LRB_PREC_SPLIT_FP16_S4)))
     for form in (W.FORM_T, W.FORM_O):
         wb = W.wide_range(form, batch=batch, device=dev)
         f = wb.flops()
         ab = wb.alg_bytes()
+        m, n = int(wb.m[0]), int(wb.n[0])
         row = {}
-        for name, prec in (("fp64", L.LRB_PREC_FP64), ("bf16_s3", L.LRB_PREC_SPLIT_BF16_S3),
-                           ("bf16_s4", L.LRB_PREC_SPLIT_BF16_S4), ("fp16_s3", L.LRB_PREC_SPLIT_FP16_S3),
-                           ("fp16_s4", L.LRB_PREC_SPLIT_FP16_S4)):
-            with handle.plan(L.descs_for(wb), precision=prec, use_graph=(prec == L.LRB_PREC_FP64)) as p:
-                steps = 2 if prec == L.LRB_PREC_FP64 else 5
+        ref = None
+        for name, opts in paths:
+            with handle.plan(L.descs_for(wb), **opts) as p:
+                wb.C.zero_()
+                p.launch()
+                torch.cuda.synchronize()
+                prod = wb.C.view(batch, m * n)
+                if ref is None:
+                    ref = prod.clone()
+                    rnorm = ref.norm(dim=1)
+                    err_all, err_max = 0.0, 0.0
+                else:
+                    d = (prod - ref).norm(dim=1)
+                    err_all = float(d.norm() / rnorm.norm())
+                    err_max = float((d / rnorm).max())
+                steps = 2 if name.startswith("fp64") else 5
                 ms, _ = timed(lambda s: p.launch(s), steps, 3)
                 st = p.status()
             ms /= steps
             row[name] = {"ms": round(ms, 3), "gflops_fp64_equiv": round(f / ms / 1e6, 1),
                          "hbm_gbs_alg": round(ab / ms / 1e6, 1), "frac_hbm": round(ab / ms / 1e6 / hbm, 4),
+                         "rel_fro_err_vs_fp64": float(f"{err_all:.3g}"), "max_entry_rel_err_vs_fp64": float(f"{err_max:.3g}"),
                          "status": int(st)}
         res["T" if form == W.FORM_T else "O"] = row
-        del wb
+        del wb, ref
         torch.cuda.empty_cache()
-    return {"workload": f"b 1024, r 64, {batch} entries, 10^U(-4,4) N(0,1), seed 4", "hbm_peak_gbs": hbm, **res}
+    return {"workload": f"b 1024, r 64, {batch} entries, 10^U(-4,4) N(0,1), seed 4; errors on one application to "
+                        f"C = 0 against the FP64 DFMA path", "hbm_peak_gbs": hbm, **res}
 
 
-def serving_leg(L, handle, dev, peak_fp64, budget=40 << 30):
+def serving_leg(L, handle, dev, peak_fp64, secs=60.0, overload_secs=10.0, budget=40 << 30):
     """Poisson request streams into the continuous-batching queue.  Each
     request: 1..512 products, b log-uniform [64, 2048], r in {8..128}, T/O
     50/50; operands are views into a 4 GB device pool, results go to a 64 GB
     device ring.  Offered loads: 0.25 / 0.5 / 0.75 / 0.9 x the FP64 capacity
-    (FP64 peak / mean request flops) for 3 s each, the stated overload rates
-    1k / 2k / 5k / 10k / 20k req/s for 0.5 s each (waiting FIFO limited to 32
-    so the backlog drains quickly), and 0.9 x the FP64 capacity once more with
-    split-precision (BF16, S = 3) waves; 40 GB admission budget, 4 stream
-    slots."""
+    (FP64 peak / mean request flops) for `secs` each, the stated overload rates
+    1k / 2k / 5k / 10k / 20k req/s for `overload_secs` each (waiting FIFO
+    limited to 32), and 0.9 x the FP64 capacity once more with split-precision
+    (BF16, S = 3) waves; 40 GB admission budget, 4 stream slots.  p50/p99 are
+    over every completed request of a point (submission -> completion), and
+    `completed` is that sample count."""
     import torch
     from paper_2311_07602_gb300 import workloads as W
     g = torch.Generator(device=dev)
@@ -685,14 +864,16 @@ def serving_leg(L, handle, dev, peak_fp64, budget=40 << 30):
     _, probe = W.serving_requests(2000, 1.0, seed=55)
     mean_flops = float(np.mean([np.sum(2.0 * bb.astype(np.float64) ** 2 * rr) for _, bb, rr in probe]))
     capacity = 0.98 * peak_fp64 * 1e12 / mean_flops
-    points = [(f"{fr:g}x capacity", fr * capacity, 3.0, 4096, L.LRB_PREC_FP64) for fr in (0.25, 0.5, 0.75, 0.9)]
-    points += [(f"{r // 1000}k req/s", float(r), 0.5, 32, L.LRB_PREC_FP64) for r in (1000, 2000, 5000, 10000, 20000)]
-    points += [("0.9x FP64 capacity, split BF16 S=3 waves", 0.9 * capacity, 3.0, 4096, L.LRB_PREC_SPLIT_BF16_S3)]
+    points = [(f"{fr:g}x capacity", fr * capacity, secs, 4096, L.LRB_PREC_FP64) for fr in (0.25, 0.5, 0.75, 0.9)]
+    points += [(f"{r // 1000}k req/s", float(r), overload_secs, 32, L.LRB_PREC_FP64)
+               for r in (1000, 2000, 5000, 10000, 20000)]
+    points += [("0.9x FP64 capacity, split BF16 S=3 waves", 0.9 * capacity, min(secs, 20.0), 4096,
+                L.LRB_PREC_SPLIT_BF16_S3)]
     rng = np.random.default_rng(505)
     cursor = 0
     results = []
-    for idx, (label, rate, secs, max_waiting, prec) in enumerate(points):
-        count = max(4, int(rate * secs))
+    for idx, (label, rate, dur, max_waiting, prec) in enumerate(points):
+        count = max(4, int(rate * dur))
         arrivals, reqs = W.serving_requests(count, rate, seed=500 + idx)
         descs = []
         for forms, bs, rs in reqs:
@@ -737,7 +918,8 @@ def serving_leg(L, handle, dev, peak_fp64, budget=40 << 30):
                         "submitted": count, "accepted": int(st["accepted"]),
                         "rejected_queue_full": int(st["rejected_full"]), "rejected_budget": int(st["rejected_budget"]),
                         "completed": int(st["completed"]), "p50_ms": round(st["p50_ms"], 3),
-                        "p99_ms": round(st["p99_ms"], 3), "sustained_gflops": round(st["gflops"], 1),
+                        "p99_ms": round(st["p99_ms"], 3), "max_ms": round(st["max_ms"], 3),
+                        "sustained_gflops": round(st["gflops"], 1),
                         "waves": int(st["waves"]), "max_concurrent_waves": int(st["max_concurrent_waves"]),
                         "mean_wave_entries": round(st["mean_wave_entries"], 1),
                         "peak_reserved_gb": round(st["peak_reserved_bytes"] / 1e9, 2)})
@@ -749,64 +931,115 @@ def serving_leg(L, handle, dev, peak_fp64, budget=40 << 30):
             "points": results}
 
 
-def e2e_leg(L, handle, batches, flops, args, barrier, max_over_ranks, world, stream):
-    """Same workload through lrb_execute_host: inputs in pinned host memory,
-    host->device copies, the launch and the device->host copy of every C in
-    the timed region.  With N ranks every rank takes the first 1/N of each
-    group (host memory is shared by the ranks), and flops count what ran."""
+def e2e_leg(L, batches, steps, warmup, barrier, max_over_ranks, world, dev_index, props, strong, sum_over_ranks):
+    """The same work through lrb_execute_host: the operands in pinned host
+    memory, their host->device copies, the launches and the device->host copy
+    of every C in the timed region (the call returns after host C holds the
+    result).  With N ranks in weak scaling every rank takes the first 1/N of
+    each batch's entries (host memory is shared by the ranks); flops count
+    what ran.  Also reported: the per-engine breakdown of the last call
+    (lrb_execute_host_get_timing), the pinned-copy rates of a single large
+    copy each way, and where the pinned pages live relative to the GPU."""
     import torch
-    rows = []
-    hold = []
+    handle = L.Handle(dev_index)
+    rows, hold = [], []
     h2d = d2h = 0
     fl = 0.0
-    for b in batches:
-        cnt = max(1, len(b) // world)
-        ea, eb, ec = (int(b.offA[cnt - 1] + b.lda[cnt - 1] * b.k[cnt - 1]), int(b.offB[cnt - 1] + b.ldb[cnt - 1] *
-                      b.n[cnt - 1]), int(b.offC[cnt - 1] + b.ldc[cnt - 1] * b.n[cnt - 1]))
-        A = torch.empty(ea, dtype=torch.float64, pin_memory=True)
-        B = torch.empty(eb, dtype=torch.float64, pin_memory=True)
-        C = torch.empty(ec, dtype=torch.float64, pin_memory=True)
-        A.copy_(b.A[:ea])
-        B.copy_(b.B[:eb])
-        C.copy_(b.C[:ec])
-        hold.append((A, B, C))
-        sub = type(b)(A, B, C, b.m[:cnt], b.n[:cnt], b.k[:cnt], b.lda[:cnt], b.ldb[:cnt], b.ldc[:cnt], b.offA[:cnt],
-                      b.offB[:cnt], b.offC[:cnt])
-        rows.append(L.descs_for(sub))
-        h2d += 8 * (A.numel() + B.numel() + C.numel())
-        d2h += 8 * C.numel()
-        fl += sub.flops()
+    topo = host_topology(props)
+    pages = {}
+    for bi, b in enumerate(batches):
+        cnt = len(b) if (world == 1 or strong) else max(1, len(b) // world)
+        sel = np.arange(cnt)
+        host = {}
+        ends = {}
+        for key, off, ld, cols in (("A", b.offA, b.lda, b.k), ("B", b.offB, b.ldb, b.n), ("C", b.offC, b.ldc, b.n)):
+            t = getattr(b, key)
+            end = int(np.max(off[sel] + ld[sel].astype(np.int64) * cols[sel]))
+            ends[t.data_ptr()] = max(ends.get(t.data_ptr(), 0), end)
+        for key in ("A", "B", "C"):
+            t = getattr(b, key)
+            if t.data_ptr() in host:
+                continue
+            n_el = ends[t.data_ptr()]
+            hb = torch.empty(n_el, dtype=torch.float64, pin_memory=True)
+            hb.copy_(t[:n_el])
+            host[t.data_ptr()] = hb
+            hold.append(hb)
+            if bi == 0:
+                pages[key] = page_nodes(hb.data_ptr(), 8 * n_el)
+        hA, hB, hC = (host[getattr(b, key).data_ptr()] for key in ("A", "B", "C"))
+        d = np.zeros(cnt, dtype=L.DESC_DTYPE)
+        d["A"] = np.uint64(hA.data_ptr()) + 8 * b.offA[sel].astype(np.uint64)
+        d["B"] = np.uint64(hB.data_ptr()) + 8 * b.offB[sel].astype(np.uint64)
+        d["C"] = np.uint64(hC.data_ptr()) + 8 * b.offC[sel].astype(np.uint64)
+        for key in ("m", "n", "k", "lda", "ldb", "ldc"):
+            d[key] = getattr(b, key)[sel]
+        rows.append(d)
+        m, n, k = (getattr(b, key)[sel].astype(np.float64) for key in ("m", "n", "k"))
+        fl += float(np.sum(2.0 * m * n * k))
     descs = np.concatenate(rows)
-    # the box's pinned-copy bandwidth in this run (context for the e2e figure):
-    # the largest A buffer in, then out, each timed alone with CUDA events
-    big = max((h[0] for h in hold), key=lambda t: t.numel())
-    dbuf = torch.empty(big.numel(), dtype=torch.float64, device="cuda")
+    # the box's pinned-copy rates in this run (context for the e2e figure):
+    # the largest pinned buffer (up to 4 GB) in, then out, then both at once
+    nel = (4 << 30) // 8
+    src = torch.zeros(nel, dtype=torch.float64, pin_memory=True)
+    dbuf = torch.zeros(nel, dtype=torch.float64, device="cuda")
+    dbuf2 = torch.zeros(nel, dtype=torch.float64, device="cuda")
     copy_gbs = {}
-    for name, dst, src in (("h2d", dbuf, big), ("d2h", big, dbuf)):
-        dst.copy_(src, non_blocking=True)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        dst.copy_(src, non_blocking=True)
-        e1.record()
-        torch.cuda.synchronize()
-        copy_gbs[name] = round(8 * big.numel() / (e0.elapsed_time(e1) / 1e3) / 1e9, 1)
-    del dbuf
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    for name in ("h2d", "d2h", "both"):
+        for rep in range(2):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s_in.wait_event(e0)
+            s_out.wait_event(e0)
+            if name in ("h2d", "both"):
+                with torch.cuda.stream(s_in):
+                    dbuf.copy_(src, non_blocking=True)
+            if name in ("d2h", "both"):
+                with torch.cuda.stream(s_out):
+                    src.copy_(dbuf2, non_blocking=True)
+            torch.cuda.current_stream().wait_stream(s_in)
+            torch.cuda.current_stream().wait_stream(s_out)
+            e1.record()
+            torch.cuda.synchronize()
+        copy_gbs[name] = round((2 if name == "both" else 1) * 8 * nel / (e0.elapsed_time(e1) / 1e3) / 1e9, 1)
+    del dbuf, dbuf2, src
     torch.cuda.synchronize()
-    for _ in range(args.warmup):
+    handle.set_host_timing(True)
+    stream = torch.cuda.Stream()
+    for _ in range(warmup):
         handle.execute_host(descs, stream)
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
+    for _ in range(steps):
         handle.execute_host(descs, stream)
     torch.cuda.synchronize()
     barrier()
     secs = max_over_ranks(time.perf_counter() - t0)
+    tm = handle.host_timing()
+    handle.close()
+    h2d = int(tm["h2d_bytes"])
+    d2h = int(tm["d2h_bytes"])
+    all_fl = sum_over_ranks(fl) if strong else world * fl
     del hold
-    return {"value": round(world * fl * args.e2e_steps / secs / 1e9, 2), "unit": UNIT,
-            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps,
-            "flops_per_step_per_rank": fl, "pinned_copy_gbs": copy_gbs,
+    if hasattr(torch._C, "_host_emptyCache"):
+        torch._C._host_emptyCache()          # hand the pinned buffers back before the next leg
+    return {"value": round(all_fl * steps / secs / 1e9, 2), "unit": UNIT,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
+            "flops_per_step_per_rank": fl,
+            "last_call": {"wall_ms": round(tm["wall_ms"], 1), "pieces": int(tm["pieces"]),
+                          "h2d_busy_ms": round(tm["h2d_busy_ms"], 1), "compute_busy_ms": round(tm["compute_busy_ms"], 1),
+                          "d2h_busy_ms": round(tm["d2h_busy_ms"], 1),
+                          "h2d_gbs": round(tm["h2d_bytes"] / max(tm["h2d_busy_ms"], 1e-9) / 1e6, 1),
+                          "d2h_gbs": round(tm["d2h_bytes"] / max(tm["d2h_busy_ms"], 1e-9) / 1e6, 1),
+                          "overlap_h2d_compute_ms": round(tm["overlap_h2d_compute_ms"], 1),
+                          "overlap_d2h_compute_ms": round(tm["overlap_d2h_compute_ms"], 1),
+                          "overlap_h2d_d2h_ms": round(tm["overlap_h2d_d2h_ms"], 1),
+                          "first_launch_after_ms": round(tm["compute_start_ms"], 1),
+                          "copies_after_last_launch_ms": round(tm["compute_end_to_last_ms"], 1)},
+            "pinned_copy_gbs": copy_gbs, "host": topo, "pinned_page_nodes": pages,
             "api": "lrb_execute_host (pinned host buffers; copies in, compute and copies out pipelined in pieces)"}
 
 

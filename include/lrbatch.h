@@ -158,15 +158,48 @@ lrb_status lrb_plan_destroy(lrb_plan* p);
  * pointers (pinned memory gives full copy speed; pageable works).  Copies
  * A, B and C into a handle-owned device arena (entries packed with tight
  * leading dimensions; runs of host-contiguous tight entries move in one copy;
- * an operand whose pointer and shape repeat an earlier entry's is copied
- * once), runs the batch in up to 64 pieces whose copies in, launches and
- * copies out overlap on three streams (the layout and plans are cached and
- * reused while the shape list repeats), copies every C back and synchronises
- * `stream`.  Returns after host C holds the result.  Not thread-safe per
+ * A and B operands whose host byte ranges overlap -- views into one operand
+ * pool, or one block shared by several entries -- are served from a single
+ * copy of the union of their ranges and keep their leading dimensions), runs
+ * the batch in up to 64 pieces whose copies in, launches and copies out
+ * overlap on three streams (each piece's three steps are enqueued together;
+ * the layout and plans are cached and reused while the descriptor list
+ * repeats), copies every C back and synchronises `stream`.  Returns after host C holds the result.  Not thread-safe per
  * handle; the arena grows to the largest batch seen and is freed by
  * lrb_destroy. */
 lrb_status lrb_execute_host(lrb_handle* h, const lrb_gemm_desc* host_descs, size_t count,
                             const lrb_plan_opts* opts, void* stream);
+
+/* Where the time of lrb_execute_host goes.  With timing enabled on a handle
+ * (off by default; it adds six timing events per piece), every call records
+ * when each piece's copies in, launch and copies out started and ended on the
+ * device, and lrb_execute_host_get_timing returns the last call's summary:
+ * busy time of each engine (the union of its intervals), the pairwise
+ * overlaps, the bytes copied each way (achieved copy rate = bytes / busy
+ * time), when the first launch started (the exposed first copy in) and how
+ * long the copies ran after the last launch ended.  Times are ms on the
+ * device clock; wall_ms spans the first interval's start to the last one's
+ * end.  get_timing returns LRB_ERR_INVALID before the first timed call. */
+typedef struct lrb_host_timing {
+    int32_t valid, pieces;
+    double wall_ms;
+    double h2d_busy_ms, compute_busy_ms, d2h_busy_ms;
+    double h2d_bytes, d2h_bytes;
+    double overlap_h2d_compute_ms, overlap_d2h_compute_ms, overlap_h2d_d2h_ms;
+    double compute_start_ms;          /* first launch start - first copy start */
+    double compute_end_to_last_ms;    /* last copy end - last launch end */
+} lrb_host_timing;
+lrb_status lrb_execute_host_set_timing(lrb_handle* h, int32_t enable);
+lrb_status lrb_execute_host_get_timing(const lrb_handle* h, lrb_host_timing* out);
+
+/* Measures the FP64 pipe's throughput on `device`: one launch of a kernel in
+ * which every thread of a full-GPU grid runs eight independent binary64 FMA
+ * chains for `iters` steps, timed with CUDA events (after a short warm-up
+ * launch).  Writes the achieved TFLOP/s (2 flops per FMA) and the launch's
+ * ms.  The library's FP64 kernels are bound by this pipe, so this is their
+ * roofline denominator measured at whatever clock the GPU runs at.
+ * Synchronous; allocates no device memory. */
+lrb_status lrb_fp64_peak_probe(int device, long long iters, double* tflops, double* ms);
 
 /* Host-only: the argument checks lrb_plan_create performs, without a GPU.
  * LRB_ERR_INVALID for null pointers, count == 0, m/n/k <= 0, ld < rows,
@@ -214,6 +247,40 @@ typedef struct lrb_lr_desc {
 lrb_status lrb_lr_plan_create(lrb_handle* h, const lrb_lr_desc* host_descs, size_t count, int32_t fused,
                               lrb_plan** out);
 
+/* ---- several GPUs ----------------------------------------------------------
+ * Batch entries are independent (Alg. 2, loop 1 runs over independent
+ * blocks), so a batch spreads over GPUs by partitioning its entries; no data
+ * moves between devices and no collective is needed.
+ *
+ * lrb_partition_lpt: host-only longest-processing-time partition of `count`
+ * items with costs cost[0..count) (e.g. 2 m n k per entry) into `parts` parts:
+ * items in order of decreasing cost (ties: lower index first), each to the
+ * part with the least load so far (ties: lower part).  Writes each item's part
+ * to part_of[count] and, if part_load is not NULL, every part's total cost to
+ * part_load[parts].  Deterministic: every process computes the same partition
+ * from the same costs, so ranks agree without exchanging anything.
+ * LRB_ERR_INVALID for NULL arrays, count == 0, parts < 1 or a negative or
+ * non-finite cost. */
+lrb_status lrb_partition_lpt(const double* cost, size_t count, int32_t parts, int32_t* part_of, double* part_load);
+
+/* A batch planned over several devices: entries are partitioned with
+ * lrb_partition_lpt over their flops 2 m n k across the `n_handles` handles
+ * (handle i gets part i) and each handle plans its share with
+ * lrb_plan_create (same opts; the descriptors of part i must point at memory
+ * that handle i's device can access -- place each entry's operands by the
+ * partition first).  A part that receives no entries has no plan.
+ * lrb_multi_launch enqueues every part's launch on streams[i] (a stream of
+ * handle i's device; NULL entries mean that device's legacy default stream),
+ * with no synchronisation between parts.  lrb_multi_plan_part reports part
+ * i's entry count and its plan summary (entries = 0 and a zeroed summary for
+ * an empty part). */
+typedef struct lrb_multi_plan lrb_multi_plan;
+lrb_status lrb_multi_plan_create(lrb_handle* const* handles, int32_t n_handles, const lrb_gemm_desc* host_descs,
+                                 size_t count, const lrb_plan_opts* opts, lrb_multi_plan** out);
+lrb_status lrb_multi_launch(lrb_multi_plan* mp, void* const* streams);
+lrb_status lrb_multi_plan_part(const lrb_multi_plan* mp, int32_t part, lrb_plan_info* info);
+lrb_status lrb_multi_plan_destroy(lrb_multi_plan* mp);
+
 /* ---- launch without device allocation -----------------------------------
  * The paper has no counterpart: this serves callers that cannot call
  * cudaMalloc (their GPU memory is owned by a framework pool or a fixed
@@ -227,7 +294,8 @@ lrb_status lrb_lr_plan_create(lrb_handle* h, const lrb_lr_desc* host_descs, size
  * return LRB_ERR_INVALID before any CUDA call.  The array (about 4.2 MB) is
  * held on every GPU that loads the library until the process exits.  All
  * calls share it, so calls that overlap on the GPU race: order them on one
- * stream.  The first call on a device looks up the array's address and the
+ * stream (calls from several host threads on one stream are kept whole by
+ * an internal lock).  The first call on a device looks up the array's address and the
  * kernel's limits; make it before any stream capture.  Asynchronous like
  * lrb_launch (the descriptor array is copied before the call returns). */
 #define LRB_NOALLOC_MAX_ENTRIES 4096

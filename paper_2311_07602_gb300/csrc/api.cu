@@ -16,6 +16,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <queue>
 #include <sstream>
 #include <string>
 #include <tuple>
@@ -199,6 +200,62 @@ int heuristic_variant(int m, int n, int k, bool dmma_ok) {
 }  // namespace
 
 namespace {
+// Summary of one timed lrb_execute_host call from per-piece intervals (ms from
+// the call's start) of the three engines: 0 copies in, 1 launches, 2 copies out.
+// Busy time = length of an engine's union of intervals; overlap of two engines
+// = length of the intersection of their unions.
+lrb_host_timing summarize_host_timing(std::vector<std::pair<double, double>> (&iv)[3], int pieces, double h2d_bytes,
+                                      double d2h_bytes) {
+    std::vector<std::pair<double, double>> u[3];
+    for (int c = 0; c < 3; ++c) {
+        std::vector<std::pair<double, double>> v = iv[c];
+        std::sort(v.begin(), v.end());
+        for (const auto& x : v) {
+            if (x.second <= x.first) continue;
+            if (!u[c].empty() && x.first <= u[c].back().second)
+                u[c].back().second = std::max(u[c].back().second, x.second);
+            else
+                u[c].push_back(x);
+        }
+    }
+    auto length = [](const std::vector<std::pair<double, double>>& a) {
+        double t = 0;
+        for (const auto& x : a) t += x.second - x.first;
+        return t;
+    };
+    auto overlap = [](const std::vector<std::pair<double, double>>& a, const std::vector<std::pair<double, double>>& b) {
+        double t = 0;
+        size_t i = 0, j = 0;
+        while (i < a.size() && j < b.size()) {
+            const double lo = std::max(a[i].first, b[j].first), hi = std::min(a[i].second, b[j].second);
+            if (hi > lo) t += hi - lo;
+            if (a[i].second < b[j].second) ++i; else ++j;
+        }
+        return t;
+    };
+    lrb_host_timing t{};
+    t.valid = 1;
+    t.pieces = pieces;
+    double lo = 1e300, hi = 0;
+    for (int c = 0; c < 3; ++c)
+        for (const auto& x : u[c]) {
+            lo = std::min(lo, x.first);
+            hi = std::max(hi, x.second);
+        }
+    t.wall_ms = hi > lo ? hi - lo : 0.0;
+    t.h2d_busy_ms = length(u[0]);
+    t.compute_busy_ms = length(u[1]);
+    t.d2h_busy_ms = length(u[2]);
+    t.h2d_bytes = h2d_bytes;
+    t.d2h_bytes = d2h_bytes;
+    t.overlap_h2d_compute_ms = overlap(u[0], u[1]);
+    t.overlap_d2h_compute_ms = overlap(u[2], u[1]);
+    t.overlap_h2d_d2h_ms = overlap(u[0], u[2]);
+    t.compute_start_ms = u[1].empty() ? 0.0 : u[1].front().first - lo;
+    t.compute_end_to_last_ms = u[1].empty() ? 0.0 : hi - u[1].back().second;
+    return t;
+}
+
 // One host<->device copy of lrb_execute_host: a 2-D block, or a merged 1-D run.
 struct HostCopy {
     const double* host;
@@ -235,6 +292,18 @@ struct lrb_handle {
     cudaStream_t copy_in = nullptr, copy_out = nullptr, compute2 = nullptr;
     std::vector<cudaEvent_t> ev_in, ev_done;
     cudaEvent_t ev_join = nullptr;
+    // optional per-piece timing of lrb_execute_host (lrb_execute_host_set_timing):
+    // per piece, start/end of its copies in, its launch and its copies out
+    bool timing = false;
+    std::vector<cudaEvent_t> tev;     // 6 per piece
+    cudaEvent_t tev0 = nullptr;       // the call's start, on the caller's stream
+    lrb_host_timing last_timing{};
+};
+
+struct lrb_multi_plan {
+    std::vector<lrb_plan*> plans;     // one per handle (NULL: the part got no entries)
+    std::vector<int64_t> entries;
+    std::vector<int> devices;
 };
 
 struct lrb_plan {
@@ -470,6 +539,7 @@ lrb_status lrb::plan_variants(lrb_handle* h, const lrb_gemm_desc* d, size_t coun
 void lrb::plan_tiles(const lrb_gemm_desc* d, size_t count, const std::vector<int>& var, std::vector<Item>& items) {
     make_tiles(d, count, var, items);
 }
+int lrb::untuned_variant(int m, int n, int k) { return heuristic_variant(m, n, k, false); }
 lrb::HandleInfo lrb::handle_info(const lrb_handle* h) {
     return HandleInfo{h->device, h->sms, h->blocks_per_sm, h->blocks_per_sm_wide, h->blocks_per_sm_slim};
 }
@@ -578,6 +648,8 @@ lrb_status lrb_destroy(lrb_handle* h) {
     if (h->copy_out) cudaStreamDestroy(h->copy_out);
     if (h->compute2) cudaStreamDestroy(h->compute2);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
+    for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
+    if (h->tev0) cudaEventDestroy(h->tev0);
     if (h->arena) cudaFree(h->arena);
     if (h->scratch) cudaFree(h->scratch);
     if (h->stream) cudaStreamDestroy(h->stream);
@@ -830,16 +902,63 @@ lrb_status lrb_execute_host(lrb_handle* h, const lrb_gemm_desc* host_descs, size
         }
         const int P = (int)cut.size() - 1;
 
-        // Device layout: piece by piece, A blocks then B blocks then C blocks,
-        // each packed with ld = rows.  An A or B block whose (pointer, rows,
-        // cols, ld) repeats an earlier one is shared (copied by the first piece).
+        // Shared regions: A and B operands whose host byte ranges overlap
+        // another A or B operand's (views into one operand pool, or one block
+        // used by several entries) are served from a single copy of the union
+        // of those ranges, made by the first piece that uses it; those entries
+        // keep their leading dimensions.  Read-only operands may overlap, so
+        // this copies each host byte once.
+        struct Span {
+            uintptr_t lo, hi;
+            size_t op;   // 2 e + 0 (A) or 1 (B)
+        };
+        struct Region {
+            uintptr_t lo, hi;
+            size_t dev;
+            int first_piece;
+        };
+        std::vector<Span> spans(2 * count);
+        for (size_t e = 0; e < count; ++e) {
+            const lrb_gemm_desc& x = host_descs[e];
+            spans[2 * e] = Span{(uintptr_t)x.A, (uintptr_t)x.A + 8 * ((size_t)x.lda * (x.k - 1) + x.m), 2 * e};
+            spans[2 * e + 1] = Span{(uintptr_t)x.B, (uintptr_t)x.B + 8 * ((size_t)x.ldb * (x.n - 1) + x.k), 2 * e + 1};
+        }
+        std::sort(spans.begin(), spans.end(), [](const Span& a, const Span& b) { return a.lo < b.lo; });
+        std::vector<int> region_of(2 * count, -1);
+        std::vector<Region> regions;
+        for (size_t i = 0; i < spans.size();) {
+            size_t j = i + 1;
+            uintptr_t hi = spans[i].hi;
+            while (j < spans.size() && spans[j].lo < hi) hi = std::max(hi, spans[j++].hi);
+            if (j - i >= 2) {
+                for (size_t t = i; t < j; ++t) region_of[spans[t].op] = (int)regions.size();
+                regions.push_back(Region{spans[i].lo, hi, 0, -1});
+            }
+            i = j;
+        }
+        std::vector<size_t> piece_of(count);
+        for (int pc = 0; pc < P; ++pc)
+            for (size_t e = cut[pc]; e < cut[pc + 1]; ++e) piece_of[e] = (size_t)pc;
+        for (size_t op = 0; op < 2 * count; ++op)
+            if (region_of[op] >= 0 && regions[region_of[op]].first_piece < 0)
+                regions[region_of[op]].first_piece = (int)piece_of[op / 2];
+
+        // Device layout, piece by piece: the shared regions the piece is first
+        // to use, then its other A blocks, B blocks and C blocks, each packed
+        // with ld = rows (runs of host-contiguous tight blocks move in one copy).
         using Copy = HostCopy;
         std::vector<lrb_gemm_desc> dd(host_descs, host_descs + count);
         std::vector<std::vector<Copy>> h2d(P), d2h(P);
         std::vector<size_t> wa(count), wb(count), wc(count);
-        std::map<std::tuple<uintptr_t, int, int, int>, size_t> seen;
         size_t cursor = 0;
         for (int pc = 0; pc < P; ++pc) {
+            for (Region& r : regions)
+                if (r.first_piece == pc) {
+                    const size_t elems = (r.hi - r.lo) / 8;
+                    r.dev = cursor;
+                    h2d[pc].push_back(Copy{(const double*)r.lo, cursor, 0, -1, 0, elems});
+                    cursor += elems;
+                }
             for (int cls = 0; cls < 3; ++cls) {
                 std::vector<Copy>& list = h2d[pc];
                 const size_t cls_start = list.size();   // runs never merge across operand classes
@@ -850,13 +969,10 @@ lrb_status lrb_execute_host(lrb_handle* h, const lrb_gemm_desc* host_descs, size
                     const int cols = cls == 0 ? x.k : cls == 1 ? x.n : x.n;
                     const int ld = cls == 0 ? x.lda : cls == 1 ? x.ldb : x.ldc;
                     std::vector<size_t>& where = cls == 0 ? wa : cls == 1 ? wb : wc;
-                    if (cls < 2) {
-                        auto it = seen.find(std::make_tuple((uintptr_t)ptr, rows, cols, ld));
-                        if (it != seen.end()) {
-                            where[e] = it->second;
-                            continue;
-                        }
-                        seen[std::make_tuple((uintptr_t)ptr, rows, cols, ld)] = cursor;
+                    if (cls < 2 && region_of[2 * e + cls] >= 0) {
+                        const Region& r = regions[region_of[2 * e + cls]];
+                        where[e] = r.dev + ((uintptr_t)ptr - r.lo) / 8;
+                        continue;
                     }
                     const size_t elems = (size_t)rows * cols;
                     where[e] = cursor;
@@ -909,8 +1025,8 @@ lrb_status lrb_execute_host(lrb_handle* h, const lrb_gemm_desc* host_descs, size
             dd[e].A = base + wa[e];
             dd[e].B = base + wb[e];
             dd[e].C = base + wc[e];
-            dd[e].lda = dd[e].m;
-            dd[e].ldb = dd[e].k;
+            if (region_of[2 * e] < 0) dd[e].lda = dd[e].m;       // packed; a shared region keeps the caller's ld
+            if (region_of[2 * e + 1] < 0) dd[e].ldb = dd[e].k;
             dd[e].ldc = dd[e].m;
         }
         const bool same = !h->host_plans.empty() && h->host_key.size() == count && h->host_cut == cut &&
@@ -957,31 +1073,178 @@ lrb_status lrb_execute_host(lrb_handle* h, const lrb_gemm_desc* host_descs, size
                       : cudaMemcpy2DAsync((void*)c.host, (size_t)c.ld * 8, dptr, (size_t)c.rows * 8,
                                           (size_t)c.rows * 8, c.cols, cudaMemcpyDeviceToHost, cs);
     };
-    // the copy streams start after work already queued on the caller's stream
+    const bool timed = h->timing;
+    if (timed) {
+        if (!h->tev0) LRB_CUDA(cudaEventCreate(&h->tev0));
+        while ((int)h->tev.size() < 6 * P) {
+            cudaEvent_t ev;
+            LRB_CUDA(cudaEventCreate(&ev));
+            h->tev.push_back(ev);
+        }
+        LRB_CUDA(cudaEventRecord(h->tev0, s));
+    }
+    // per piece: tev[6 pc + 0/1] copies in start/end, + 2/3 launch, + 4/5 copies out
+    auto mark = [&](int pc, int which, cudaStream_t cs) -> cudaError_t {
+        return timed ? cudaEventRecord(h->tev[6 * pc + which], cs) : cudaSuccess;
+    };
+    // the copy and compute streams start after work already queued on the
+    // caller's stream
     LRB_CUDA(cudaEventRecord(h->ev_done[0], s));
     LRB_CUDA(cudaStreamWaitEvent(h->copy_in, h->ev_done[0], 0));
+    LRB_CUDA(cudaStreamWaitEvent(h->compute2, h->ev_done[0], 0));
+    // Each piece's copies in, launch and copies out are enqueued together, so
+    // that when the host blocks in a copy call (a stream holds a bounded
+    // number of pending operations) every earlier piece's launch is already
+    // queued.  Pieces alternate between the caller's stream and a second
+    // compute stream, so one piece's last tiles overlap the next piece's first.
     for (int pc = 0; pc < P; ++pc) {
+        LRB_CUDA(mark(pc, 0, h->copy_in));
         for (const HostCopy& c : h2d[pc]) LRB_CUDA(copy(c, true, h->copy_in));
         LRB_CUDA(cudaEventRecord(h->ev_in[pc], h->copy_in));
-    }
-    // pieces alternate between the caller's stream and a second compute
-    // stream, so one piece's last tiles overlap the next piece's first ones
-    LRB_CUDA(cudaStreamWaitEvent(h->compute2, h->ev_done[0], 0));
-    for (int pc = 0; pc < P; ++pc) {
+        LRB_CUDA(mark(pc, 1, h->copy_in));
         cudaStream_t cs = (pc & 1) ? h->compute2 : s;
         LRB_CUDA(cudaStreamWaitEvent(cs, h->ev_in[pc], 0));
+        LRB_CUDA(mark(pc, 2, cs));
         st = lrb_launch(h->host_plans[pc], (void*)cs);
         if (st != LRB_OK) return st;
+        LRB_CUDA(mark(pc, 3, cs));
         LRB_CUDA(cudaEventRecord(h->ev_done[pc], cs));
         LRB_CUDA(cudaStreamWaitEvent(h->copy_out, h->ev_done[pc], 0));
+        LRB_CUDA(mark(pc, 4, h->copy_out));
         for (const HostCopy& c : d2h[pc]) LRB_CUDA(copy(c, false, h->copy_out));
+        LRB_CUDA(mark(pc, 5, h->copy_out));
     }
     // the caller's stream ends after everything, as before
     LRB_CUDA(cudaEventRecord(h->ev_join, h->copy_out));
     LRB_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
     LRB_CUDA(cudaStreamSynchronize(h->copy_out));
     LRB_CUDA(cudaStreamSynchronize(s));
+    if (timed) {
+        std::vector<std::pair<double, double>> iv[3];
+        for (int pc = 0; pc < P; ++pc)
+            for (int cls = 0; cls < 3; ++cls) {
+                float a = 0.f, b = 0.f;
+                LRB_CUDA(cudaEventElapsedTime(&a, h->tev0, h->tev[6 * pc + 2 * cls]));
+                LRB_CUDA(cudaEventElapsedTime(&b, h->tev0, h->tev[6 * pc + 2 * cls + 1]));
+                iv[cls].emplace_back(a, b);
+            }
+        double bytes[2] = {0.0, 0.0};
+        for (int pc = 0; pc < P; ++pc) {
+            for (const HostCopy& c : h2d[pc]) bytes[0] += 8.0 * (double)c.elems;
+            for (const HostCopy& c : d2h[pc]) bytes[1] += 8.0 * (double)c.elems;
+        }
+        h->last_timing = summarize_host_timing(iv, P, bytes[0], bytes[1]);
+    }
     return LRB_OK;
+}
+
+lrb_status lrb_execute_host_set_timing(lrb_handle* h, int32_t enable) {
+    if (!h) return fail(LRB_ERR_INVALID, "handle is NULL");
+    h->timing = enable != 0;
+    return LRB_OK;
+}
+
+lrb_status lrb_execute_host_get_timing(const lrb_handle* h, lrb_host_timing* out) {
+    if (!h || !out) return fail(LRB_ERR_INVALID, "handle or out is NULL");
+    if (!h->last_timing.valid) return fail(LRB_ERR_INVALID, "no timed lrb_execute_host call yet");
+    *out = h->last_timing;
+    return LRB_OK;
+}
+
+lrb_status lrb_partition_lpt(const double* cost, size_t count, int32_t parts, int32_t* part_of, double* part_load) {
+    if (!cost || !part_of || count == 0 || parts < 1)
+        return fail(LRB_ERR_INVALID, "lrb_partition_lpt: NULL array, count == 0 or parts < 1");
+    for (size_t i = 0; i < count; ++i)
+        if (!(cost[i] >= 0.0) || !std::isfinite(cost[i])) return fail(LRB_ERR_INVALID, "lrb_partition_lpt: bad cost");
+    std::vector<size_t> order(count);
+    for (size_t i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+    // min-heap of (load, part): the least-loaded part, lower part index on ties
+    using Slot = std::pair<double, int32_t>;
+    std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
+    for (int32_t r = 0; r < parts; ++r) heap.push(Slot(0.0, r));
+    std::vector<double> load(parts, 0.0);
+    for (size_t i : order) {
+        Slot s = heap.top();
+        heap.pop();
+        part_of[i] = s.second;
+        s.first = s.first + cost[i];
+        load[s.second] = s.first;
+        heap.push(s);
+    }
+    if (part_load)
+        for (int32_t r = 0; r < parts; ++r) part_load[r] = load[r];
+    return LRB_OK;
+}
+
+lrb_status lrb_multi_plan_create(lrb_handle* const* handles, int32_t n_handles, const lrb_gemm_desc* host_descs,
+                                 size_t count, const lrb_plan_opts* opts, lrb_multi_plan** out) {
+    if (!out) return fail(LRB_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!handles || n_handles < 1) return fail(LRB_ERR_INVALID, "no handles");
+    for (int32_t i = 0; i < n_handles; ++i)
+        if (!handles[i]) return fail(LRB_ERR_INVALID, "a handle is NULL");
+    const lrb_plan_opts o = opts ? *opts : default_opts();
+    lrb_status st = validate(host_descs, count, o);
+    if (st != LRB_OK) return st;
+    std::vector<double> cost(count);
+    for (size_t e = 0; e < count; ++e)
+        cost[e] = 2.0 * (double)host_descs[e].m * (double)host_descs[e].n * (double)host_descs[e].k;
+    std::vector<int32_t> part(count);
+    st = lrb_partition_lpt(cost.data(), count, n_handles, part.data(), nullptr);
+    if (st != LRB_OK) return st;
+    lrb_multi_plan* mp = new (std::nothrow) lrb_multi_plan();
+    if (!mp) return fail(LRB_ERR_NOMEM, "multi-plan allocation");
+    mp->plans.assign(n_handles, nullptr);
+    mp->entries.assign(n_handles, 0);
+    mp->devices.resize(n_handles);
+    for (int32_t i = 0; i < n_handles; ++i) {
+        mp->devices[i] = handles[i]->device;
+        std::vector<lrb_gemm_desc> mine;
+        for (size_t e = 0; e < count; ++e)
+            if (part[e] == i) mine.push_back(host_descs[e]);
+        mp->entries[i] = (int64_t)mine.size();
+        if (mine.empty()) continue;
+        st = lrb_plan_create(handles[i], mine.data(), mine.size(), &o, &mp->plans[i]);
+        if (st != LRB_OK) {
+            lrb_multi_plan_destroy(mp);
+            return st;
+        }
+    }
+    *out = mp;
+    return LRB_OK;
+}
+
+lrb_status lrb_multi_launch(lrb_multi_plan* mp, void* const* streams) {
+    if (!mp) return fail(LRB_ERR_INVALID, "multi-plan is NULL");
+    for (size_t i = 0; i < mp->plans.size(); ++i) {
+        if (!mp->plans[i]) continue;
+        lrb_status st = lrb_launch(mp->plans[i], streams ? streams[i] : nullptr);
+        if (st != LRB_OK) return st;
+    }
+    return LRB_OK;
+}
+
+lrb_status lrb_multi_plan_part(const lrb_multi_plan* mp, int32_t part, lrb_plan_info* info) {
+    if (!mp || !info) return fail(LRB_ERR_INVALID, "multi-plan or info is NULL");
+    if (part < 0 || part >= (int32_t)mp->plans.size()) return fail(LRB_ERR_INVALID, "part out of range");
+    if (!mp->plans[part]) {
+        std::memset(info, 0, sizeof(*info));
+        return LRB_OK;
+    }
+    return lrb_plan_get_info(mp->plans[part], info);
+}
+
+lrb_status lrb_multi_plan_destroy(lrb_multi_plan* mp) {
+    if (!mp) return fail(LRB_ERR_INVALID, "multi-plan is NULL");
+    lrb_status st = LRB_OK;
+    for (lrb_plan* p : mp->plans)
+        if (p) {
+            lrb_status s2 = lrb_plan_destroy(p);
+            if (st == LRB_OK) st = s2;
+        }
+    delete mp;
+    return st;
 }
 
 lrb_status lrb_plan_status(lrb_plan* p) {

@@ -95,6 +95,9 @@ lrb_status plan_variants(lrb_handle* h, const lrb_gemm_desc* d, size_t count, co
 // Enqueues an FP64 plan's persistent launch on `s` (no device switch: safe
 // inside a stream capture); cudaErrorInvalidValue for other plan kinds.
 cudaError_t enqueue_fp64_plan(lrb_plan* p, cudaStream_t s);
+// The planner's tile variant for an entry when nothing is tuned (by output
+// width: 64 x 8, 64 x 16, 64 x 32 or 64 x 64 tiles, variants 0..3).
+int untuned_variant(int m, int n, int k);
 // Output tiles of all entries, longest first.
 void plan_tiles(const lrb_gemm_desc* d, size_t count, const std::vector<int>& var, std::vector<Item>& items);
 

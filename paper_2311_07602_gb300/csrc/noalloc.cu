@@ -13,8 +13,14 @@
 // Limits: at most kMaxEntries entries and kMaxTiles output tiles per call
 // (about 4.2 MB of scratch, held by every GPU that loads the library until
 // the process exits).  Every call shares the array: calls that overlap on
-// the GPU (different streams, or another thread) race on it, so callers must
-// order them.  The first call on a device looks up the array's device
+// the GPU (calls on different streams) race on it, so callers must order
+// them, e.g. on one stream.  A lock keeps each call's three enqueued steps
+// (descriptor copy, tile kernel, persistent launch) together, so calls from
+// several host threads on one stream stay whole and ordered.  The tile rule
+// and tile extents are the planner's (checked on every call), so the tiles
+// are those of a planned launch with untuned tiles (lrb_plan_create with
+// tune = 0) on a batch big enough that the planner keeps its 64-row tiles.
+// The first call on a device looks up the array's device
 // address (cudaGetSymbolAddress) and sets the kernel's shared-memory limit;
 // make that first call before any stream capture.
 #include <algorithm>
@@ -36,36 +42,69 @@ static_assert(kOffItems % 256 == 0, "tile list alignment");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-// Untuned tile choice, the same rule as the planner's (by output width n).
-__host__ __device__ inline int untuned_variant(int n) {
-    return n <= 8 ? 0 : n <= 16 ? 1 : n <= 32 ? 2 : 3;
-}
-__host__ __device__ inline int variant_bm(int) { return 64; }
-__host__ __device__ inline int variant_bn(int v) { return v == 0 ? 8 : v == 1 ? 16 : v == 2 ? 32 : 64; }
+// Tile extents of the variants the untuned rule can pick (0..3), copied from
+// the planner's variant table at set-up and passed to the tile kernel, so the
+// tile list always matches the planner's tiles for those variants.
+constexpr int kUntunedVariants = 4;
+struct TileShapes {
+    int bm[kUntunedVariants], bn[kUntunedVariants];
+};
 
-// One block: per-entry tile offsets (serial prefix in shared memory), then
-// every thread writes tiles; clears the work counter.
-__global__ void __launch_bounds__(256) k_noalloc_tiles(const DevDesc* __restrict__ descs, int count,
-                                                       Item* __restrict__ items, int* __restrict__ head) {
-    __shared__ int s_off[kMaxEntries + 1];
-    if (threadIdx.x == 0) {
-        int acc = 0;
-        for (int e = 0; e < count; ++e) {
-            s_off[e] = acc;
-            const int v = untuned_variant(descs[e].n);
-            acc += ((descs[e].m + variant_bm(v) - 1) / variant_bm(v)) * ((descs[e].n + variant_bn(v) - 1) / variant_bn(v));
-        }
-        s_off[count] = acc;
+// One block of kTileThreads threads.  Each thread takes a run of consecutive
+// entries, picks their variants (the planner's untuned rule, by output width)
+// and counts their tiles; a block-wide scan of those counts gives every
+// entry's first tile (kept in shared memory); then thread t writes tiles t,
+// t + kTileThreads, ..., finding each tile's entry by binary search over the
+// first-tile offsets, and thread 0 clears the work counter.
+constexpr int kTileThreads = 256;
+constexpr int kPerThread = (kMaxEntries + kTileThreads - 1) / kTileThreads;
+
+__host__ __device__ __forceinline__ int noalloc_variant(int n) { return n <= 8 ? 0 : n <= 16 ? 1 : n <= 32 ? 2 : 3; }
+inline int noalloc_variant_host(int n) { return noalloc_variant(n); }
+
+__global__ void __launch_bounds__(kTileThreads) k_noalloc_tiles(const DevDesc* __restrict__ descs, int count,
+                                                                TileShapes shp, Item* __restrict__ items,
+                                                                int* __restrict__ head) {
+    __shared__ int s_scan[kTileThreads];
+    __shared__ int s_first[kMaxEntries + 1];
+    const int t = threadIdx.x;
+    const int e0 = min(count, t * kPerThread), e1 = min(count, e0 + kPerThread);
+    int mine = 0;
+    for (int e = e0; e < e1; ++e) {
+        const int v = noalloc_variant(descs[e].n);
+        mine += ((descs[e].m + shp.bm[v] - 1) / shp.bm[v]) * ((descs[e].n + shp.bn[v] - 1) / shp.bn[v]);
+    }
+    s_scan[t] = mine;
+    __syncthreads();
+    // inclusive scan (Hillis-Steele) over the per-thread tile counts
+    for (int o = 1; o < kTileThreads; o <<= 1) {
+        const int x = t >= o ? s_scan[t - o] : 0;
+        __syncthreads();
+        s_scan[t] += x;
+        __syncthreads();
+    }
+    int first = s_scan[t] - mine;
+    for (int e = e0; e < e1; ++e) {
+        s_first[e] = first;
+        const int v = noalloc_variant(descs[e].n);
+        first += ((descs[e].m + shp.bm[v] - 1) / shp.bm[v]) * ((descs[e].n + shp.bn[v] - 1) / shp.bn[v]);
+    }
+    const int total = s_scan[kTileThreads - 1];
+    if (t == 0) {
+        s_first[count] = total;
         *head = 0;
     }
     __syncthreads();
-    for (int e = 0; e < count; ++e) {
-        const int v = untuned_variant(descs[e].n);
-        const int bm = variant_bm(v), bn = variant_bn(v);
-        const int tm = (descs[e].m + bm - 1) / bm;
-        const int n_t = s_off[e + 1] - s_off[e];
-        for (int t = threadIdx.x; t < n_t; t += blockDim.x)
-            items[s_off[e] + t] = Item{e, (t % tm) * bm, (t / tm) * bn, v};
+    for (int i = t; i < total; i += kTileThreads) {
+        int lo = 0, hi = count;          // the last entry e with s_first[e] <= i (entries of 0 tiles do not exist)
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s_first[mid] <= i) lo = mid; else hi = mid;
+        }
+        const int e = lo, v = noalloc_variant(descs[e].n);
+        const int bm = shp.bm[v], bn = shp.bn[v];
+        const int tm = (descs[e].m + bm - 1) / bm, r = i - s_first[e];
+        items[i] = Item{e, (r % tm) * bm, (r / tm) * bn, v};
     }
 }
 
@@ -75,6 +114,10 @@ struct DeviceSetup {
 };
 std::mutex g_setup_mu;
 DeviceSetup g_setup[128];
+// Held while one call enqueues its copy, tile kernel and launch, so that two
+// host threads calling on the same stream cannot interleave those three
+// steps (each call's steps then stay together in stream order).
+std::mutex g_enqueue_mu;
 
 }  // namespace
 }  // namespace lrb
@@ -90,11 +133,20 @@ extern "C" lrb_status lrb_launch_noalloc(const lrb_gemm_desc* host_descs, size_t
     }
     lrb_status st = lrb_validate(host_descs, count, nullptr);
     if (st != LRB_OK) return st;
+    TileShapes shp;
+    for (int v = 0; v < kUntunedVariants; ++v) {
+        shp.bm[v] = kVariants[v].bm();
+        shp.bn[v] = kVariants[v].bn();
+    }
     long long tiles = 0;
     for (size_t e = 0; e < count; ++e) {
-        const int v = untuned_variant(host_descs[e].n);
-        tiles += (long long)((host_descs[e].m + variant_bm(v) - 1) / variant_bm(v)) *
-                 ((host_descs[e].n + variant_bn(v) - 1) / variant_bn(v));
+        const lrb_gemm_desc& x = host_descs[e];
+        const int v = untuned_variant(x.m, x.n, x.k);
+        if (v < 0 || v >= kUntunedVariants || v != noalloc_variant_host(x.n)) {
+            set_last_error("lrb_launch_noalloc: the planner's untuned tile rule changed; update the tile kernel");
+            return LRB_ERR_UNSUPPORTED;
+        }
+        tiles += (long long)((x.m + shp.bm[v] - 1) / shp.bm[v]) * ((x.n + shp.bn[v] - 1) / shp.bn[v]);
     }
     if (tiles > kMaxTiles) {
         std::snprintf(msg, sizeof msg, "lrb_launch_noalloc: %lld output tiles exceed the maximum of %d", tiles,
@@ -128,13 +180,14 @@ extern "C" lrb_status lrb_launch_noalloc(const lrb_gemm_desc* host_descs, size_t
         su = g_setup[dev];
     }
     cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> enqueue_lock(g_enqueue_mu);
     char* base = (char*)su.scratch;
     int* d_head = (int*)(base + kOffHead);
     DevDesc* d_descs = (DevDesc*)(base + kOffDescs);
     Item* d_items = (Item*)(base + kOffItems);
     cudaError_t e = cudaMemcpyAsync(d_descs, host_descs, sizeof(DevDesc) * count, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
-        k_noalloc_tiles<<<1, 256, 0, s>>>(d_descs, (int)count, d_items, d_head);
+        k_noalloc_tiles<<<1, kTileThreads, 0, s>>>(d_descs, (int)count, shp, d_items, d_head);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {

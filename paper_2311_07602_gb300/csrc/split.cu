@@ -182,16 +182,108 @@ __device__ __forceinline__ uint16_t digit_bits(int d) {
     }
 }
 
-// Exact binary64 of I 2^X for |I| < 2^53, built from the bits.
+// Exact binary64 of I 2^X for |I| < 2^53, built from the bits: |I| shifted
+// so its leading one sits at bit 52, plus (exponent - 1) << 52 (the leading
+// one then completes the exponent field), plus the sign.
+// Results outside binary64's normal range (never for operands of ordinary
+// size): a real call, so the compiler cannot predicate these FP64
+// instructions into the common path, where they would occupy the FP64 pipe.
+__device__ __noinline__ double scaled_int_to_double_rare(long long I, int X) { return ldexp((double)I, X); }
+
 __device__ __forceinline__ double scaled_int_to_double(long long I, int X) {
     if (I == 0) return 0.0;
     const unsigned long long u = (unsigned long long)(I < 0 ? -I : I);
     const int lz = __clzll((long long)u);
     const int biased = 1023 + (63 - lz) + X;
-    if (biased <= 0 || biased >= 2047) return ldexp((double)I, X);   // out of the normal range
-    const unsigned long long mant = (u << (lz - 11)) & 0xFFFFFFFFFFFFFull;
-    const unsigned long long b = (I < 0 ? (1ull << 63) : 0ull) | ((unsigned long long)biased << 52) | mant;
+    if (biased <= 0 || biased >= 2047) return scaled_int_to_double_rare(I, X);
+    const unsigned long long b = (u << (lz - 11)) + ((unsigned long long)(biased - 1) << 52) +
+                                 (I < 0 ? (1ull << 63) : 0ull);
     return __longlong_as_double((long long)b);
+}
+
+// ---- the 32-bit digit path (BF16, S = 3) ------------------------------------
+// Key of a row of A within a chunk: the largest hi word of |a| (sign cleared),
+// with bit 0 set when any lo word is nonzero.  The maximum's exponent field is
+// key >> 20, so for key >= kKeyFastMin (a normal maximum of at least 2^-997)
+// E = (key >> 20) - 1022, and key == 0 means every value is +-0; other keys
+// (rows of values below 2^-997) take the exact 64-bit path.
+constexpr uint32_t kKeyFastMin = 26u << 20;
+__device__ __forceinline__ bool key_fast(uint32_t key) { return key == 0u || key >= kKeyFastMin; }
+__device__ __forceinline__ int key_exponent(uint32_t key) { return key ? (int)(key >> 20) - 1022 : 0; }
+// The right shift of an element with exponent field ef is key_shift(key) - ef
+// (>= 8 in the row; a zero row shifts every element out).
+__device__ __forceinline__ int key_shift(uint32_t key) { return key ? (int)(key >> 20) + 8 : (1 << 20); }
+
+// The balanced digits of a (BF16, S = 3) for a row with key_fast(key), as
+// floats whose top 16 bits are the BF16 patterns; the same digits as
+// make_digits<3, 8>.  Z = RN_even(a 2^(24 - E)) on 32-bit words: T holds the
+// top 32 bits of the 53-bit significand, the lower 21 bits folded into T's
+// lowest bit as a sticky bit (the rounding position, bit sh - 1 >= 7, lies
+// above it); (T + 2^(sh-1) - 1 + bit sh of T) >> sh, in 33-bit arithmetic, is
+// the round-to-nearest-even of T / 2^sh; a shift beyond 32 leaves less than a
+// quarter unit, which rounds to 0.  Z + 0x8080 carries the two lower balanced
+// digits into bytes (each digit + 128), d_1 is the rest; a digit d becomes the
+// float 1.5 2^23 + d by placing it into that constant's bit pattern, minus the
+// constant.
+__device__ __forceinline__ void digits_bf16_s3(double a, int ksh, float& f1, float& f2, float& f3) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(a);
+    const uint32_t h = (uint32_t)(bits >> 32), l = (uint32_t)bits;
+    uint32_t T = __funnelshift_l(l, h, 11);
+    T |= min(l << 11, 1u) | 0x80000000u;
+    const int sh = ksh - (int)((h >> 20) & 0x7FFu);
+    const uint32_t hm1 = __funnelshift_rc(0xFFFFFFFFu, 0u, (uint32_t)(33 - sh));   // 2^(sh-1) - 1
+    const uint32_t lsb = __funnelshift_rc(T, 0u, (uint32_t)sh) & 1u;
+    const unsigned long long v = (unsigned long long)T + hm1 + lsb;
+    const uint32_t Z = __funnelshift_rc((uint32_t)v, (uint32_t)(v >> 32), (uint32_t)sh);
+    const int mult = sh <= 32 ? (((int)h >> 31) | 1) : 0;
+    const int Zp = (int)Z * mult + 0x8080;
+    f3 = __int_as_float((int)__byte_perm((uint32_t)Zp, 0x4B400000u, 0x7650)) - 12583040.0f;
+    f2 = __int_as_float((int)__byte_perm((uint32_t)Zp, 0x4B400000u, 0x7651)) - 12583040.0f;
+    f1 = __int_as_float(0x4B400000 + (Zp >> 16)) - 12582912.0f;
+}
+
+// Largest |P_L| one k-chunk can produce for level L (kc times the level's
+// kept pairs' largest digit products; max|d_1| = 2^beta, max|d_s| = 2^(beta-1)).
+template <bool FP16, int S>
+__host__ __device__ constexpr long long level_bound_c(int L) {
+    const int beta = FP16 ? 9 : 8, kc = FP16 ? 32 : 64;
+    long long b = 0;
+    for (int s = 1; s <= S; ++s)
+        for (int t = 1; t <= S; ++t)
+            if (s + t == L && s + t <= S + 1) b += (long long)(s == 1 ? 1 << beta : 1 << (beta - 1)) * (t == 1 ? 1 << beta : 1 << (beta - 1));
+    return b * kc;
+}
+
+// Level sum L = l + 2 of an FP32 accumulator as an integer.  Where |P_L| <=
+// 2^22 the float P + 1.5 2^23 is exact and its bit pattern is 0x4B400000 + P
+// (an FP32 add, no conversion instruction); larger bounds convert.
+template <bool FP16, int S>
+__device__ __forceinline__ int level_value(uint32_t v, int l) {
+    if (level_bound_c<FP16, S>(l + 2) <= (1ll << 22))
+        return __float_as_int(__uint_as_float(v) + 12582912.0f) - 0x4B400000;
+    return __float2int_rn(__uint_as_float(v));
+}
+
+// I = sum_L P_L 2^(beta (S + 1 - L)) of one output (levels L = l + 2 in
+// v[l]).  BF16: the two lowest levels combine in 32 bits (|P_L 2^8 + P_L'| <
+// 2^31), as do the two highest for S = 4, and one wide multiply-add joins them.
+template <bool FP16, int S, int RC>
+__device__ __forceinline__ long long level_integer(const uint32_t (&v)[S][RC], int jj) {
+    if constexpr (!FP16 && S == 3) {
+        const int hi = level_value<FP16, S>(v[0][jj], 0);
+        const int lo = level_value<FP16, S>(v[1][jj], 1) * 256 + level_value<FP16, S>(v[2][jj], 2);
+        return (long long)hi * 65536 + lo;
+    } else if constexpr (!FP16 && S == 4) {
+        const int hi = level_value<FP16, S>(v[0][jj], 0) * 256 + level_value<FP16, S>(v[1][jj], 1);
+        const int lo = level_value<FP16, S>(v[2][jj], 2) * 256 + level_value<FP16, S>(v[3][jj], 3);
+        return (long long)hi * 65536 + lo;
+    } else {
+        constexpr int BETA = FP16 ? 9 : 8;
+        long long I = 0;
+#pragma unroll
+        for (int l = 0; l < S; ++l) I = I * (1ll << BETA) + level_value<FP16, S>(v[l][jj], l);
+        return I;
+    }
 }
 
 // The B part of one chunk, by 512 threads (warp w: columns 4w .. 4w + 3; lane:
@@ -321,10 +413,12 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* src) {
 // One CTA per SM, 512 threads, tiles taken round-robin (tile = 128 x 64
 // outputs).  The k-chunks of all of a CTA's tiles form one pipeline: while
 // the tensor cores run chunk i (digit planes and TMEM accumulator set i&1),
-// the threads recombine chunk i-1 from the other TMEM set and then load and
-// slice chunk i+1.  Thread t: row 32 (w % 4) + lane of the tile (w = warp,
-// = its TMEM lane), quarter q = w / 4 of the chunk's columns for slicing and
-// of the tile's 64 output columns for recombination.
+// the threads recombine chunk i-1 from the other TMEM set.  The operands of
+// chunk i+1 are loaded into registers as soon as chunk i's digits are in
+// shared memory, so their latency hides behind chunk i's tensor-core issue
+// and chunk i-1's recombination.  Thread t: row 32 (w % 4) + lane of the tile
+// (w = warp, = its TMEM lane), quarter q = w / 4 of the chunk's columns for
+// slicing and of the tile's 64 output columns for recombination.
 template <bool FP16, int S, int MODE>
 __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restrict__ descs,
                                                          const SItem* __restrict__ items, int n_items,
@@ -338,12 +432,17 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
     // bfirst[entry] + ct * chunks + c.  MODE 2: A too (k_slice_a), unit
     // afirst[entry] + row tile * chunks + c (entries with several column tiles).
     constexpr bool PRE = MODE >= 1;
+    constexpr bool preA = MODE == 2;
+    // A's digits on the 32-bit path (BF16, S = 3; MODE 1, the T-form path:
+    // MODE 0 also slices B and would spill registers with both paths compiled)
+    constexpr bool FAST = !FP16 && S == 3 && MODE == 1;
     using C_ = Cfg<FP16, S>;
     constexpr int BETA = C_::beta, KC = C_::kc;
     constexpr int QC = KC / 4;            // chunk columns of A per thread
     constexpr int KB = KC / 32;           // k values of B per lane and column
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ unsigned long long s_rmax[4][kTM];
+    __shared__ uint32_t s_rkey[4][kTM];
     __shared__ __align__(16) int s_E[2][kTM];
     __shared__ __align__(16) int s_F[2][kTN];
     __shared__ __align__(8) uint64_t s_bar[2];
@@ -391,6 +490,39 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
         }
     };
 
+    // The operands this thread slices for one chunk, in registers: A row
+    // m0 + rloc, chunk columns [k0 + q QC, k0 + q QC + QC); B columns 4 w ..
+    // 4 w + 3 of the tile, k values lane + 32 h.  Zero outside the entry.
+    double av[preA ? 1 : QC];
+    double bv[PRE ? 1 : 4][KB];
+    auto load_chunk = [&](const DevDesc& d, int m0, int n0, int k0) {
+        const int kcl = min(KC, d.k - k0);
+        if constexpr (!preA) {
+            const int row = m0 + rloc;
+            const double* ap = d.A + (size_t)row + (size_t)(k0 + q * QC) * (size_t)d.lda;
+            const int ncol = row < d.m ? min(QC, kcl - q * QC) : 0;   // valid columns of this quarter
+#pragma unroll
+            for (int p = 0; p < QC; ++p) {
+                av[p] = p < ncol ? __ldg(ap) : 0.0;
+                ap += d.lda;
+            }
+        }
+        if constexpr (!PRE) {
+            const int wc = min(kTN, d.n - n0);
+#pragma unroll
+            for (int jc = 0; jc < 4; ++jc) {
+                const int j = 4 * warp + jc;
+#pragma unroll
+                for (int h = 0; h < KB; ++h) {
+                    const int kk = lane + 32 * h;
+                    bv[jc][h] = (j < wc && kk < kcl)
+                                    ? __ldg(d.B + (size_t)(k0 + kk) + (size_t)(n0 + j) * (size_t)d.ldb)
+                                    : 0.0;
+                }
+            }
+        }
+    };
+
     // recombine `prev` into acc (its MMAs committed to s_bar[prev.stage])
     auto recombine = [&](uint32_t parity) -> bool {
         // warp-uniform decision before the warp-collective TMEM loads
@@ -400,25 +532,32 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
         const int E = s_E[prev.stage][rloc];
         const int row = prev.row0 + rloc;
+        // the thread's 16 output columns in groups of RC (MODE 1 holds the next
+        // chunk's operands in registers meanwhile, so it loads 4 at a time)
+        constexpr int RC = MODE == 1 ? 4 : 8;
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            uint32_t v[S][8];
+        for (int grp = 0; grp < 16 / RC; ++grp) {
+            uint32_t v[S][RC];
 #pragma unroll
             for (int l = 0; l < S; ++l) {
-                const uint32_t ta = tmem + lane_base + (uint32_t)(prev.stage * S * kTN + l * kTN + 16 * q + 8 * half);
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-                             : "=r"(v[l][0]), "=r"(v[l][1]), "=r"(v[l][2]), "=r"(v[l][3]), "=r"(v[l][4]),
-                               "=r"(v[l][5]), "=r"(v[l][6]), "=r"(v[l][7])
-                             : "r"(ta));
+                const uint32_t ta = tmem + lane_base + (uint32_t)(prev.stage * S * kTN + l * kTN + 16 * q + RC * grp);
+                if constexpr (RC == 8) {
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                                 : "=r"(v[l][0]), "=r"(v[l][1]), "=r"(v[l][2]), "=r"(v[l][3]), "=r"(v[l][4]),
+                                   "=r"(v[l][5]), "=r"(v[l][6]), "=r"(v[l][7])
+                                 : "r"(ta));
+                } else {
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+                                 : "=r"(v[l][0]), "=r"(v[l][1]), "=r"(v[l][2]), "=r"(v[l][3])
+                                 : "r"(ta));
+                }
             }
             asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
-                const int j = 16 * q + 8 * half + jj;
-                long long I = 0;
-#pragma unroll
-                for (int l = 0; l < S; ++l)   // level L = l + 2, weight 2^(beta (S - 1 - l))
-                    I = I * (1ll << BETA) + (long long)__float2int_rn(__uint_as_float(v[l][jj]));
+            for (int jj = 0; jj < RC; ++jj) {
+                const int j = 16 * q + RC * grp + jj;
+                // level L = l + 2 has weight 2^(beta (S - 1 - l))
+                const long long I = level_integer<FP16, S, RC>(v, jj);
                 if (dump != nullptr && row < prev.m && prev.col0 + j < prev.n) {
 #pragma unroll
                     for (int l = 0; l < S; ++l)
@@ -427,7 +566,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
                 }
                 // the exact binary64 value I 2^X (built from bits with integer
                 // instructions), then one binary64 add
-                acc[8 * half + jj] += scaled_int_to_double(I, E + s_F[prev.stage][j] - BETA * (S + 1));
+                acc[RC * grp + jj] += scaled_int_to_double(I, E + s_F[prev.stage][j] - BETA * (S + 1));
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -469,21 +608,20 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
     int t = blockIdx.x;
     if (t < n_items) {
         const SItem it0 = items[t];
-        load_c0(descs[it0.entry], it0.row0, it0.col0);
+        const DevDesc d0 = descs[it0.entry];
+        load_c0(d0, it0.row0, it0.col0);
+        if constexpr (MODE == 1) load_chunk(d0, it0.row0, it0.col0, 0);
     }
     while (t < n_items) {
         const SItem item = items[t];
         const DevDesc d = descs[item.entry];
         const int m0 = item.row0, n0 = item.col0;
         const int nch = (d.k + KC - 1) / KC;
-        const int row = m0 + rloc;
-        const bool row_ok = row < d.m;
-        const int wc = min(kTN, d.n - n0);
+        const int tn = t + gridDim.x;
         {
             // the CTA's next tile into L2 while this one runs: its C (one
             // 128-byte line of 16 rows per thread) and, when pre-sliced, its
             // first chunk's digit units
-            const int tn = t + gridDim.x;
             if (tn < n_items) {
                 const SItem nx = items[tn];
                 const DevDesc dn = descs[nx.entry];
@@ -507,66 +645,52 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
         for (int c = 0; c < nch; ++c, ++iter) {
             const int stage = iter & 1;
             const int k0 = c * KC;
-            const int kcl = min(KC, d.k - k0);
             uint8_t* planeA = smem + stage * (S * (C_::planeA + C_::planeB));
             uint8_t* planeB = planeA + S * C_::planeA;
-            constexpr bool pre = PRE;
-            constexpr bool preA = MODE == 2;
             // (0) pre-sliced units.  MODE 1 copies this chunk's B here, where the
-            // copy overlaps the loads and slicing of A; MODE 2 (nothing else to
-            // overlap) copies the next chunk's units one iteration ahead (step 6),
-            // so only the CTA's first chunk copies its own here.
+            // copy overlaps the slicing of A; MODE 2 (nothing else to overlap)
+            // copies the next chunk's units one iteration ahead (step 6), so
+            // only the CTA's first chunk copies its own here.
             if constexpr (PRE) {
                 if (MODE == 1 || iter == 0) copy_units(item.entry, m0, n0, nch, c, stage);
             }
-            // (1) loads: A row `row`, chunk columns [q QC, q QC + QC); B columns 4 w .. 4 w + 3
-            double av[preA ? 1 : QC];
-            if constexpr (!preA) {
-                const double* ap = d.A + (size_t)row + (size_t)(k0 + q * QC) * (size_t)d.lda;
-                const int ncol = row_ok ? min(QC, kcl - q * QC) : 0;   // valid columns of this quarter
-#pragma unroll
-                for (int p = 0; p < QC; ++p) {
-                    av[p] = p < ncol ? __ldg(ap) : 0.0;
-                    ap += d.lda;
-                }
-            }
-            double bv[PRE ? 1 : 4][KB];
-            if constexpr (!PRE) {
-#pragma unroll
-                for (int jc = 0; jc < 4; ++jc) {
-                    const int j = 4 * warp + jc;
-#pragma unroll
-                    for (int h = 0; h < KB; ++h) {
-                        const int kk = lane + 32 * h;
-                        bv[jc][h] = (j < wc && kk < kcl)
-                                        ? __ldg(d.B + (size_t)(k0 + kk) + (size_t)(n0 + j) * (size_t)d.ldb)
-                                        : 0.0;
-                    }
-                }
-            }
-            // (1b) the tile's next chunk into L2 while this one is sliced and the
-            // previous one recombined: one 128-byte line per thread (A: 16 rows
-            // of one column; B: 16 k of one column), in-bounds addresses only
-            if (c + 1 < nch) {
-                const int kn = k0 + KC;
+            if constexpr (MODE == 0) load_chunk(d, m0, n0, k0);
+            // (1) a later chunk into L2 (MODE 1: the one after the next, whose
+            // loads step 3b issues; MODE 0: the next): one 128-byte line per
+            // thread (A: 16 rows of one column; B: 16 k of one column),
+            // in-bounds addresses only
+            if (c + (MODE == 0 ? 1 : 2) < nch) {
+                const int kn = k0 + (MODE == 0 ? 1 : 2) * KC;
                 const int kk = tid >> 3, r = m0 + 16 * (tid & 7);
                 if (!preA && kk < KC && kn + kk < d.k && r < d.m)
                     asm volatile("prefetch.global.L2 [%0];\n" ::"l"(d.A + (size_t)r + (size_t)(kn + kk) * (size_t)d.lda));
                 if (!PRE && tid < kTN * (KC / 16)) {
                     const int j = tid / (KC / 16), kb = kn + 16 * (tid % (KC / 16));
-                    if (j < wc && kb < d.k)
+                    if (j < min(kTN, d.n - n0) && kb < d.k)
                         asm volatile("prefetch.global.L2 [%0];\n" ::"l"(d.B + (size_t)kb + (size_t)(n0 + j) * (size_t)d.ldb));
                 }
             }
-            // (2) exponents
+            // (2) exponents: A's row maxima over the four quarters through shared
+            // memory, B's column maxima by warp shuffles
             if constexpr (!preA) {
-                unsigned long long mx = 0;
+                if constexpr (FAST) {
+                    uint32_t mx = 0, lo = 0;
 #pragma unroll
-                for (int p = 0; p < QC; ++p) {
-                    const unsigned long long v = (unsigned long long)__double_as_longlong(av[p]) & 0x7FFFFFFFFFFFFFFFull;
-                    mx = v > mx ? v : mx;
+                    for (int p = 0; p < QC; ++p) {
+                        const unsigned long long b = (unsigned long long)__double_as_longlong(av[p]);
+                        mx = max(mx, (uint32_t)(b >> 32) & 0x7FFFFFFFu);
+                        lo |= (uint32_t)b;
+                    }
+                    s_rkey[q][rloc] = mx | (lo != 0u ? 1u : 0u);
+                } else {
+                    unsigned long long mx = 0;
+#pragma unroll
+                    for (int p = 0; p < QC; ++p) {
+                        const unsigned long long v = (unsigned long long)__double_as_longlong(av[p]) & 0x7FFFFFFFFFFFFFFFull;
+                        mx = v > mx ? v : mx;
+                    }
+                    s_rmax[q][rloc] = mx;
                 }
-                s_rmax[q][rloc] = mx;
             }
             if constexpr (!PRE) {
 #pragma unroll
@@ -586,36 +710,80 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
                     if (lane == 0) s_F[stage][4 * warp + jc] = mx ? exp_of_bits(mx) : 0;
                 }
             }
-            if (!(preA && pre)) __syncthreads();   // row / column exponents exchanged
-            int E = 0;
+            if (!(preA && PRE)) __syncthreads();   // row / column exponents exchanged
+            int E = 0, ksh = 0;
+            bool slow = !FAST;
             if constexpr (!preA) {
-                unsigned long long mx = s_rmax[0][rloc];
+                if constexpr (FAST) {
+                    const uint32_t key = max(max(s_rkey[0][rloc], s_rkey[1][rloc]), max(s_rkey[2][rloc], s_rkey[3][rloc]));
+                    // rows of values below 2^-997 (CTA-uniform decision): the
+                    // exact 64-bit maxima and digits for this chunk
+                    slow = __syncthreads_or(!key_fast(key)) != 0;
+                    if (!slow) {
+                        E = key_exponent(key);
+                        ksh = key_shift(key);
+                    } else {
+                        unsigned long long mx = 0;
 #pragma unroll
-                for (int qq = 1; qq < 4; ++qq) mx = s_rmax[qq][rloc] > mx ? s_rmax[qq][rloc] : mx;
-                E = mx ? exp_of_bits(mx) : 0;
+                        for (int p = 0; p < QC; ++p) {
+                            const unsigned long long v = (unsigned long long)__double_as_longlong(av[p]) & 0x7FFFFFFFFFFFFFFFull;
+                            mx = v > mx ? v : mx;
+                        }
+                        s_rmax[q][rloc] = mx;
+                        __syncthreads();
+                    }
+                }
+                if (slow) {
+                    unsigned long long mx = s_rmax[0][rloc];
+#pragma unroll
+                    for (int qq = 1; qq < 4; ++qq) mx = s_rmax[qq][rloc] > mx ? s_rmax[qq][rloc] : mx;
+                    E = mx ? exp_of_bits(mx) : 0;
+                }
                 if (q == 0) s_E[stage][rloc] = E;
             }
             // (3) digits into the planes of this stage (free: their MMAs were
             // waited for when the previous chunk was recombined)
             if constexpr (!preA) {
                 uint8_t* dst = planeA + (rloc >> 3) * C_::sbo + (rloc & 7) * 16 + (q * QC / 8) * 128;
+                if (!slow) {
+                    if constexpr (FAST) {
 #pragma unroll
-                for (int g = 0; g < QC / 8; ++g) {
-                    uint32_t packed[S][4];
+                        for (int g = 0; g < QC / 8; ++g) {
+                            uint32_t packed[3][4];
 #pragma unroll
-                    for (int p = 0; p < 8; p += 2) {
-                        int d0[S], d1[S];
-                        make_digits<S, BETA>(av[8 * g + p], E, d0);
-                        make_digits<S, BETA>(av[8 * g + p + 1], E, d1);
+                            for (int p = 0; p < 8; p += 2) {
+                                float a1, a2, a3, b1, b2, b3;
+                                digits_bf16_s3(av[8 * g + p], ksh, a1, a2, a3);
+                                digits_bf16_s3(av[8 * g + p + 1], ksh, b1, b2, b3);
+                                packed[0][p >> 1] = __byte_perm(__float_as_uint(a1), __float_as_uint(b1), 0x7632);
+                                packed[1][p >> 1] = __byte_perm(__float_as_uint(a2), __float_as_uint(b2), 0x7632);
+                                packed[2][p >> 1] = __byte_perm(__float_as_uint(a3), __float_as_uint(b3), 0x7632);
+                            }
+#pragma unroll
+                            for (int s2 = 0; s2 < 3; ++s2)
+                                *reinterpret_cast<uint4*>(dst + s2 * C_::planeA + g * 128) =
+                                    make_uint4(packed[s2][0], packed[s2][1], packed[s2][2], packed[s2][3]);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int g = 0; g < QC / 8; ++g) {
+                        uint32_t packed[S][4];
+#pragma unroll
+                        for (int p = 0; p < 8; p += 2) {
+                            int d0[S], d1[S];
+                            make_digits<S, BETA>(av[8 * g + p], E, d0);
+                            make_digits<S, BETA>(av[8 * g + p + 1], E, d1);
+#pragma unroll
+                            for (int s2 = 0; s2 < S; ++s2)
+                                packed[s2][p >> 1] =
+                                    (uint32_t)digit_bits<FP16>(d0[s2]) | ((uint32_t)digit_bits<FP16>(d1[s2]) << 16);
+                        }
 #pragma unroll
                         for (int s2 = 0; s2 < S; ++s2)
-                            packed[s2][p >> 1] =
-                                (uint32_t)digit_bits<FP16>(d0[s2]) | ((uint32_t)digit_bits<FP16>(d1[s2]) << 16);
+                            *reinterpret_cast<uint4*>(dst + s2 * C_::planeA + g * 128) =
+                                make_uint4(packed[s2][0], packed[s2][1], packed[s2][2], packed[s2][3]);
                     }
-#pragma unroll
-                    for (int s2 = 0; s2 < S; ++s2)
-                        *reinterpret_cast<uint4*>(dst + s2 * C_::planeA + g * 128) =
-                            make_uint4(packed[s2][0], packed[s2][1], packed[s2][2], packed[s2][3]);
                 }
             }
             if (PRE) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -635,6 +803,18 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
                             *reinterpret_cast<uint16_t*>(dst + s2 * C_::planeB + (kk >> 3) * 128 + (kk & 7) * 2) =
                                 digit_bits<FP16>(dg[s2]);
                     }
+                }
+            }
+            // (3b) MODE 1: the next chunk's A into registers (this chunk's
+            // digits are in shared memory), so the loads run during steps 4 and
+            // 5.  (MODE 0 also holds B and loads at the top of the iteration:
+            // keeping both live across the recombination would spill.)
+            if constexpr (MODE == 1) {
+                if (c + 1 < nch) {
+                    load_chunk(d, m0, n0, k0 + KC);
+                } else if (tn < n_items) {
+                    const SItem nx = items[tn];
+                    load_chunk(descs[nx.entry], nx.row0, nx.col0, 0);
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -689,8 +869,8 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
             if constexpr (MODE == 2) {
                 if (c + 1 < nch) {
                     copy_units(item.entry, m0, n0, nch, c + 1, stage ^ 1);
-                } else if (t + (int)gridDim.x < n_items) {
-                    const SItem nx = items[t + gridDim.x];
+                } else if (tn < n_items) {
+                    const SItem nx = items[tn];
                     copy_units(nx.entry, nx.row0, nx.col0, (descs[nx.entry].k + KC - 1) / KC, 0, stage ^ 1);
                 }
             }
@@ -706,7 +886,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
             have_prev = true;
         }
         if (failed) break;
-        t += gridDim.x;
+        t = tn;
     }
     if (have_prev && !failed) {
         const bool ok = recombine((uint32_t)(((iter - 1) >> 1) & 1));

@@ -76,6 +76,14 @@ class lrb_queue_stats_t(ctypes.Structure):
                [(n, ctypes.c_double) for n in ("p50_ms", "p99_ms", "mean_ms", "max_ms", "gflops", "flops_done")]
 
 
+class lrb_host_timing(ctypes.Structure):
+    _fields_ = [("valid", ctypes.c_int32), ("pieces", ctypes.c_int32)] + \
+               [(n, ctypes.c_double) for n in ("wall_ms", "h2d_busy_ms", "compute_busy_ms", "d2h_busy_ms",
+                                               "h2d_bytes", "d2h_bytes", "overlap_h2d_compute_ms",
+                                               "overlap_d2h_compute_ms", "overlap_h2d_d2h_ms", "compute_start_ms",
+                                               "compute_end_to_last_ms")]
+
+
 class LrbError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -122,6 +130,15 @@ def lib():
             "lrb_plan_tiles_host": ([vp, sz, i32, vp, sz, ctypes.POINTER(sz)], i32),
             "lrb_variant_count": ([], i32),
             "lrb_variant_shape": ([i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
+            "lrb_execute_host_set_timing": ([vp, i32], i32),
+            "lrb_execute_host_get_timing": ([vp, ctypes.POINTER(lrb_host_timing)], i32),
+            "lrb_fp64_peak_probe": ([ctypes.c_int, ctypes.c_longlong, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)], i32),
+            "lrb_partition_lpt": ([vp, sz, i32, vp, vp], i32),
+            "lrb_multi_plan_create": ([vp, i32, vp, sz, ctypes.POINTER(lrb_plan_opts), ctypes.POINTER(vp)], i32),
+            "lrb_multi_launch": ([vp, vp], i32),
+            "lrb_multi_plan_part": ([vp, i32, ctypes.POINTER(lrb_plan_info)], i32),
+            "lrb_multi_plan_destroy": ([vp], i32),
             "lrb_last_error": ([], ctypes.c_char_p),
         }
         for name, (args, res) in sigs.items():
@@ -224,6 +241,62 @@ def lrb_launch_noalloc(descs: np.ndarray, stream=None) -> int:
     return lib().lrb_launch_noalloc(d.ctypes.data if len(d) else None, len(d), _stream_ptr(stream))
 
 
+def lrb_partition_lpt(cost, parts: int):
+    """Longest-processing-time partition (host only): (part of each item,
+    total cost of each part)."""
+    c = np.ascontiguousarray(cost, dtype=np.float64)
+    part = np.zeros(len(c), dtype=np.int32)
+    load = np.zeros(max(parts, 1), dtype=np.float64)
+    check(lib().lrb_partition_lpt(c.ctypes.data if len(c) else None, len(c), int(parts), part.ctypes.data,
+                                  load.ctypes.data))
+    return part, load
+
+
+class MultiPlan:
+    """lrb_multi_plan_create / lrb_multi_launch / lrb_multi_plan_destroy: one
+    batch partitioned (LPT over 2 m n k) across several handles, one plan per
+    handle, launched with no synchronisation between the parts."""
+
+    def __init__(self, handles, descs: np.ndarray, **opts):
+        self.descs = np.ascontiguousarray(descs, dtype=DESC_DTYPE)
+        self.opts = make_opts(**opts)
+        self.n = len(handles)
+        arr = (ctypes.c_void_p * self.n)(*[h.ptr.value for h in handles])
+        self.ptr = ctypes.c_void_p()
+        check(lib().lrb_multi_plan_create(arr, self.n, self.descs.ctypes.data, len(self.descs), ctypes.byref(self.opts),
+                                          ctypes.byref(self.ptr)))
+
+    def launch(self, streams=None):
+        if streams is None:
+            check(lib().lrb_multi_launch(self.ptr, None))
+            return
+        arr = (ctypes.c_void_p * self.n)(*[_stream_ptr(s).value for s in streams])
+        check(lib().lrb_multi_launch(self.ptr, arr))
+
+    def part_info(self, i: int) -> dict:
+        info = lrb_plan_info()
+        check(lib().lrb_multi_plan_part(self.ptr, i, ctypes.byref(info)))
+        return {f: getattr(info, f) for f, _ in lrb_plan_info._fields_}
+
+    def close(self):
+        if self.ptr:
+            check(lib().lrb_multi_plan_destroy(self.ptr))
+            self.ptr = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def lrb_fp64_peak_probe(device: int = 0, iters: int = 1 << 20):
+    """Measured FP64-pipe throughput: (TFLOP/s, ms of the timed launch)."""
+    t, ms = ctypes.c_double(0), ctypes.c_double(0)
+    check(lib().lrb_fp64_peak_probe(device, int(iters), ctypes.byref(t), ctypes.byref(ms)))
+    return t.value, ms.value
+
+
 def lrb_variant_count() -> int:
     return lib().lrb_variant_count()
 
@@ -260,6 +333,16 @@ class Handle:
         d = np.ascontiguousarray(host_descs, dtype=DESC_DTYPE)
         o = make_opts(**opts)
         check(lib().lrb_execute_host(self.ptr, d.ctypes.data, len(d), ctypes.byref(o), _stream_ptr(stream)))
+
+    def set_host_timing(self, enable: bool = True):
+        """lrb_execute_host_set_timing: record per-piece copy/launch intervals."""
+        check(lib().lrb_execute_host_set_timing(self.ptr, int(bool(enable))))
+
+    def host_timing(self) -> dict:
+        """lrb_execute_host_get_timing: summary of the last timed execute_host call."""
+        t = lrb_host_timing()
+        check(lib().lrb_execute_host_get_timing(self.ptr, ctypes.byref(t)))
+        return {f: getattr(t, f) for f, _ in lrb_host_timing._fields_}
 
 
 class Plan:

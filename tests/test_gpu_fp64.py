@@ -249,6 +249,101 @@ def test_execute_host_pipelined_pieces(handle):
     check_entries(pinned[2].numpy().copy(), exp3, Ah, Bh, exp1, big, tol=3e-13)
 
 
+def test_execute_host_timing_summary(handle):
+    """lrb_execute_host_get_timing after a timed call: the byte counts are the
+    copies the call makes (A, B, C in; C out), every engine's busy time fits
+    in the call's span, overlaps are no longer than either engine's busy time,
+    and the result is still the oracle's."""
+    with L.Handle(0) as h:
+        with pytest.raises(L.LrbError):
+            h.host_timing()                      # nothing timed yet
+        b = W.uniform_batch(W.FORM_T, 512, 32, 256, dist="normal", seed=63)      # ~300 MB, several pieces
+        Ah, Bh, C0 = host(b.A), host(b.B), host(b.C)
+        pinned = [torch.from_numpy(x.copy()).pin_memory() for x in (Ah, Bh, C0)]
+        d = np.zeros(len(b), dtype=L.DESC_DTYPE)
+        for key, t, off in (("A", pinned[0], b.offA), ("B", pinned[1], b.offB), ("C", pinned[2], b.offC)):
+            d[key] = np.uint64(t.data_ptr()) + 8 * off.astype(np.uint64)
+        for key in ("m", "n", "k", "lda", "ldb", "ldc"):
+            d[key] = getattr(b, key)
+        h.set_host_timing(True)
+        h.execute_host(d)
+        t = h.host_timing()
+        assert t["valid"] == 1 and t["pieces"] >= 2
+        assert t["h2d_bytes"] == 8 * (Ah.size + Bh.size + C0.size)
+        assert t["d2h_bytes"] == 8 * C0.size
+        for key in ("h2d_busy_ms", "compute_busy_ms", "d2h_busy_ms"):
+            assert 0 < t[key] <= t["wall_ms"] + 1e-6
+        assert t["overlap_h2d_compute_ms"] <= min(t["h2d_busy_ms"], t["compute_busy_ms"]) + 1e-6
+        assert t["overlap_d2h_compute_ms"] <= min(t["d2h_busy_ms"], t["compute_busy_ms"]) + 1e-6
+        assert 0 <= t["compute_start_ms"] <= t["wall_ms"]
+        check_entries(pinned[2].numpy().copy(), oracle_batch(Ah, Bh, C0, b), Ah, Bh, C0, b)
+
+
+def test_execute_host_shared_pool():
+    """Entries whose A and B are overlapping views into one pinned host pool
+    (the variable-size batch's layout) and whose C are distinct: the pool's
+    span is copied once (the byte count says so), the entries keep their
+    leading dimensions, and every C matches the oracle; a second call reuses
+    the cached layout."""
+    forms, bs, rs = W.variable_shapes(120, seed=93, bmin=16, bmax=300)
+    b = W.variable_batch(forms, bs, rs, seed=93, pool_elems=1 << 20)
+    Ah, C0 = host(b.A), host(b.C)
+    pool = torch.from_numpy(Ah.copy()).pin_memory()
+    C = torch.from_numpy(C0.copy()).pin_memory()
+    d = np.zeros(len(b), dtype=L.DESC_DTYPE)
+    d["A"] = np.uint64(pool.data_ptr()) + 8 * b.offA.astype(np.uint64)
+    d["B"] = np.uint64(pool.data_ptr()) + 8 * b.offB.astype(np.uint64)
+    d["C"] = np.uint64(C.data_ptr()) + 8 * b.offC.astype(np.uint64)
+    for key in ("m", "n", "k", "lda", "ldb", "ldc"):
+        d[key] = getattr(b, key)
+    lo = min(int(b.offA.min()), int(b.offB.min()))
+    hi = max(int((b.offA + b.lda.astype(np.int64) * b.k).max()), int((b.offB + b.ldb.astype(np.int64) * b.n).max()))
+    with L.Handle(0) as h:
+        h.set_host_timing(True)
+        h.execute_host(d)
+        t = h.host_timing()
+        c_elems = int(np.sum(b.m.astype(np.int64) * b.n))
+        assert t["d2h_bytes"] == 8 * c_elems
+        assert t["h2d_bytes"] <= 8 * ((hi - lo) + c_elems)          # the pool once, not per entry
+        exp1 = oracle_batch(Ah, Ah, C0, b)
+        check_entries(C.numpy().copy(), exp1, Ah, Ah, C0, b)
+        h.execute_host(d)
+        check_entries(C.numpy().copy(), oracle_batch(Ah, Ah, exp1, b), Ah, Ah, exp1, b, tol=3e-13)
+
+
+def test_multi_plan_two_handles():
+    """lrb_multi_plan_create over two handles (both on device 0 here: every
+    call of this suite has one GPU) partitions the batch by LPT over 2 m n k,
+    each part planned and launched on its own stream with no synchronisation
+    between them; every C matches the oracle and the parts' entry counts are
+    the partition's."""
+    forms, bs, rs = W.variable_shapes(200, seed=91, bmin=16, bmax=600)
+    b = W.variable_batch(forms, bs, rs, seed=91)
+    Ah, Bh, C0 = host(b.A), host(b.B), host(b.C)
+    dev = b.to("cuda")
+    part, _ = L.lrb_partition_lpt(2.0 * b.m.astype(float) * b.n * b.k, 2)
+    with L.Handle(0) as h1, L.Handle(0) as h2:
+        with L.MultiPlan([h1, h2], L.descs_for(dev), use_graph=True) as mp:
+            assert [mp.part_info(i)["entries"] for i in range(2)] == [int(np.sum(part == i)) for i in range(2)]
+            s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+            mp.launch([s1, s2])
+            torch.cuda.synchronize()
+    check_entries(host(dev.C), oracle_batch(Ah, Bh, C0, b), Ah, Bh, C0, b)
+
+
+def test_fp64_peak_probe():
+    """The FP64-pipe probe reports a rate near the unit-count figure (SMs x 2
+    DFMA lanes x 2 flops x clock) at the GPU's clock range, and rejects bad
+    arguments."""
+    props = torch.cuda.get_device_properties(0)
+    tflops, ms = L.lrb_fp64_peak_probe(0, 1 << 16)
+    lo = props.multi_processor_count * 2 * 2 * 0.9e9 / 1e12         # at 900 MHz
+    hi = props.multi_processor_count * 2 * 2 * 2.2e9 / 1e12 * 1.05  # at 2.2 GHz, 5 % slack
+    assert ms > 0 and lo <= tflops <= hi, (tflops, lo, hi)
+    with pytest.raises(L.LrbError):
+        L.lrb_fp64_peak_probe(0, 0)
+
+
 def test_allocation_failure_is_reported(handle):
     """A host-buffer batch whose device arena cannot exist (720 GB) fails with
     LRB_ERR_NOMEM before any copy touches the (fake) host pointers."""
