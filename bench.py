@@ -1038,7 +1038,9 @@ def e2e_leg(L, batches, steps, warmup, barrier, max_over_ranks, world, dev_index
                           "overlap_d2h_compute_ms": round(tm["overlap_d2h_compute_ms"], 1),
                           "overlap_h2d_d2h_ms": round(tm["overlap_h2d_d2h_ms"], 1),
                           "first_launch_after_ms": round(tm["compute_start_ms"], 1),
-                          "copies_after_last_launch_ms": round(tm["compute_end_to_last_ms"], 1)},
+                          "copies_after_last_launch_ms": round(tm["compute_end_to_last_ms"], 1),
+                          "first_piece_h2d_ms": round(tm["first_h2d_ms"], 1),
+                          "first_piece_h2d_gb": round(tm["first_h2d_bytes"] / 1e9, 3)},
             "pinned_copy_gbs": copy_gbs, "host": topo, "pinned_page_nodes": pages,
             "api": "lrb_execute_host (pinned host buffers; copies in, compute and copies out pipelined in pieces)"}
 

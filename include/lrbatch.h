@@ -157,7 +157,9 @@ lrb_status lrb_plan_destroy(lrb_plan* p);
 /* Host-buffer form of a whole batch: the descriptors' A, B and C are HOST
  * pointers (pinned memory gives full copy speed; pageable works).  Copies
  * A, B and C into a handle-owned device arena (entries packed with tight
- * leading dimensions; runs of host-contiguous tight entries move in one copy;
+ * leading dimensions; runs of tight blocks that lie less than 256 bytes apart
+ * in host memory move in one copy -- the bytes between two C blocks of such a
+ * run are copied back unchanged, so they must not change during the call;
  * A and B operands whose host byte ranges overlap -- views into one operand
  * pool, or one block shared by several entries -- are served from a single
  * copy of the union of their ranges and keep their leading dimensions), runs
@@ -188,6 +190,7 @@ typedef struct lrb_host_timing {
     double overlap_h2d_compute_ms, overlap_d2h_compute_ms, overlap_h2d_d2h_ms;
     double compute_start_ms;          /* first launch start - first copy start */
     double compute_end_to_last_ms;    /* last copy end - last launch end */
+    double first_h2d_ms, first_h2d_bytes;   /* the first piece's copies in */
 } lrb_host_timing;
 lrb_status lrb_execute_host_set_timing(lrb_handle* h, int32_t enable);
 lrb_status lrb_execute_host_get_timing(const lrb_handle* h, lrb_host_timing* out);

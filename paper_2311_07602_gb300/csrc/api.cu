@@ -200,12 +200,20 @@ int heuristic_variant(int m, int n, int k, bool dmma_ok) {
 }  // namespace
 
 namespace {
+// lrb_execute_host merges the copies of blocks that lie at most this many
+// elements apart in host memory (256 bytes: the alignment padding between
+// blocks laid out back to back); the bytes between them are copied in and,
+// for C, written back unchanged.
+constexpr ptrdiff_t kGapElems = 32;
+// A shared operand region is copied in pieces of at most this many elements.
+constexpr size_t kRegionChunkElems = (size_t)32 << 20;
+
 // Summary of one timed lrb_execute_host call from per-piece intervals (ms from
 // the call's start) of the three engines: 0 copies in, 1 launches, 2 copies out.
 // Busy time = length of an engine's union of intervals; overlap of two engines
 // = length of the intersection of their unions.
 lrb_host_timing summarize_host_timing(std::vector<std::pair<double, double>> (&iv)[3], int pieces, double h2d_bytes,
-                                      double d2h_bytes) {
+                                      double d2h_bytes, double first_h2d_bytes) {
     std::vector<std::pair<double, double>> u[3];
     for (int c = 0; c < 3; ++c) {
         std::vector<std::pair<double, double>> v = iv[c];
@@ -253,6 +261,8 @@ lrb_host_timing summarize_host_timing(std::vector<std::pair<double, double>> (&i
     t.overlap_h2d_d2h_ms = overlap(u[0], u[2]);
     t.compute_start_ms = u[1].empty() ? 0.0 : u[1].front().first - lo;
     t.compute_end_to_last_ms = u[1].empty() ? 0.0 : hi - u[1].back().second;
+    t.first_h2d_ms = iv[0].empty() ? 0.0 : iv[0].front().second - iv[0].front().first;
+    t.first_h2d_bytes = first_h2d_bytes;
     return t;
 }
 
@@ -956,7 +966,9 @@ lrb_status lrb_execute_host(lrb_handle* h, const lrb_gemm_desc* host_descs, size
                 if (r.first_piece == pc) {
                     const size_t elems = (r.hi - r.lo) / 8;
                     r.dev = cursor;
-                    h2d[pc].push_back(Copy{(const double*)r.lo, cursor, 0, -1, 0, elems});
+                    for (size_t o = 0; o < elems; o += kRegionChunkElems)   // in chunks of 256 MB
+                        h2d[pc].push_back(Copy{(const double*)r.lo + o, cursor + o, 0, -1, 0,
+                                               std::min(kRegionChunkElems, elems - o)});
                     cursor += elems;
                 }
             for (int cls = 0; cls < 3; ++cls) {
@@ -975,19 +987,23 @@ lrb_status lrb_execute_host(lrb_handle* h, const lrb_gemm_desc* host_descs, size
                         continue;
                     }
                     const size_t elems = (size_t)rows * cols;
-                    where[e] = cursor;
-                    Copy c{ptr, cursor, rows, cols, ld, elems};
                     if (list.size() > cls_start && ld == rows) {
+                        // extend the previous run when this block starts at most
+                        // kGapElems elements after it in host memory; the device
+                        // layout keeps the same gap, so one 1-D copy moves both
                         Copy& b = list.back();
-                        if (b.ld == b.rows && b.host + b.elems == ptr && b.dev + b.elems == cursor) {
-                            b.elems += elems;
+                        const ptrdiff_t gap = ptr - (b.host + b.elems);
+                        if ((b.cols < 0 || b.ld == b.rows) && gap >= 0 && gap < kGapElems && b.dev + b.elems == cursor) {
+                            cursor += (size_t)gap;
+                            where[e] = cursor;
+                            b.elems += (size_t)gap + elems;
                             b.cols = -1;   // merged run: a 1-D copy
-                        } else {
-                            list.push_back(c);
+                            cursor += elems;
+                            continue;
                         }
-                    } else {
-                        list.push_back(c);
                     }
+                    where[e] = cursor;
+                    list.push_back(Copy{ptr, cursor, rows, cols, ld, elems});
                     cursor += elems;
                 }
                 if (cls == 2) d2h[pc].assign(list.begin() + cls_start, list.end());
@@ -1128,12 +1144,13 @@ lrb_status lrb_execute_host(lrb_handle* h, const lrb_gemm_desc* host_descs, size
                 LRB_CUDA(cudaEventElapsedTime(&b, h->tev0, h->tev[6 * pc + 2 * cls + 1]));
                 iv[cls].emplace_back(a, b);
             }
-        double bytes[2] = {0.0, 0.0};
+        double bytes[2] = {0.0, 0.0}, first = 0.0;
         for (int pc = 0; pc < P; ++pc) {
             for (const HostCopy& c : h2d[pc]) bytes[0] += 8.0 * (double)c.elems;
             for (const HostCopy& c : d2h[pc]) bytes[1] += 8.0 * (double)c.elems;
         }
-        h->last_timing = summarize_host_timing(iv, P, bytes[0], bytes[1]);
+        for (const HostCopy& c : h2d[0]) first += 8.0 * (double)c.elems;
+        h->last_timing = summarize_host_timing(iv, P, bytes[0], bytes[1], first);
     }
     return LRB_OK;
 }

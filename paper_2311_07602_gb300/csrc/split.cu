@@ -54,6 +54,8 @@ constexpr int kTM = 128;       // tile rows (MMA M)
 constexpr int kTN = 64;        // tile cols (MMA N)
 constexpr int kThreadsS = 512;
 constexpr int kTmemCols = 512; // 2 sets x S levels x 64 columns
+constexpr int kCTileBytes = 128 * 64 * 8;   // one staged C tile (MODE 2)
+constexpr int kSmemLimit = 227 * 1024;      // dynamic shared memory per CTA
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on any device-side wait
 
 struct SItem {
@@ -185,17 +187,12 @@ __device__ __forceinline__ uint16_t digit_bits(int d) {
 // Exact binary64 of I 2^X for |I| < 2^53, built from the bits: |I| shifted
 // so its leading one sits at bit 52, plus (exponent - 1) << 52 (the leading
 // one then completes the exponent field), plus the sign.
-// Results outside binary64's normal range (never for operands of ordinary
-// size): a real call, so the compiler cannot predicate these FP64
-// instructions into the common path, where they would occupy the FP64 pipe.
-__device__ __noinline__ double scaled_int_to_double_rare(long long I, int X) { return ldexp((double)I, X); }
-
 __device__ __forceinline__ double scaled_int_to_double(long long I, int X) {
     if (I == 0) return 0.0;
     const unsigned long long u = (unsigned long long)(I < 0 ? -I : I);
     const int lz = __clzll((long long)u);
     const int biased = 1023 + (63 - lz) + X;
-    if (biased <= 0 || biased >= 2047) return scaled_int_to_double_rare(I, X);
+    if (__builtin_expect(biased <= 0 || biased >= 2047, 0)) return ldexp((double)I, X);
     const unsigned long long b = (u << (lz - 11)) + ((unsigned long long)(biased - 1) << 52) +
                                  (I < 0 ? (1ull << 63) : 0ull);
     return __longlong_as_double((long long)b);
@@ -211,32 +208,36 @@ constexpr uint32_t kKeyFastMin = 26u << 20;
 __device__ __forceinline__ bool key_fast(uint32_t key) { return key == 0u || key >= kKeyFastMin; }
 __device__ __forceinline__ int key_exponent(uint32_t key) { return key ? (int)(key >> 20) - 1022 : 0; }
 // The right shift of an element with exponent field ef is key_shift(key) - ef
-// (>= 8 in the row; a zero row shifts every element out).
-__device__ __forceinline__ int key_shift(uint32_t key) { return key ? (int)(key >> 20) + 8 : (1 << 20); }
+// (>= 7 in the row; a zero row shifts every element out).
+__device__ __forceinline__ int key_shift(uint32_t key) { return key ? (int)(key >> 20) + 7 : (1 << 20); }
+
+// x >> n for n in [0, 2^32), 0 once n >= 32 (PTX shr clamps the amount).
+__device__ __forceinline__ uint32_t shr_clamped(uint32_t x, uint32_t n) {
+    uint32_t r;
+    asm("shr.b32 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(n));
+    return r;
+}
 
 // The balanced digits of a (BF16, S = 3) for a row with key_fast(key), as
 // floats whose top 16 bits are the BF16 patterns; the same digits as
-// make_digits<3, 8>.  Z = RN_even(a 2^(24 - E)) on 32-bit words: T holds the
-// top 32 bits of the 53-bit significand, the lower 21 bits folded into T's
-// lowest bit as a sticky bit (the rounding position, bit sh - 1 >= 7, lies
-// above it); (T + 2^(sh-1) - 1 + bit sh of T) >> sh, in 33-bit arithmetic, is
-// the round-to-nearest-even of T / 2^sh; a shift beyond 32 leaves less than a
-// quarter unit, which rounds to 0.  Z + 0x8080 carries the two lower balanced
-// digits into bytes (each digit + 128), d_1 is the rest; a digit d becomes the
-// float 1.5 2^23 + d by placing it into that constant's bit pattern, minus the
-// constant.
+// make_digits<3, 8>.  Z = RN_even(a 2^(24 - E)) on 32-bit words: W is a
+// 31-bit window of the significand (the implicit one at bit 30), the lower
+// 22 bits folded into W's lowest bit as a sticky bit; with sh = the window's
+// right shift (>= 7, so the rounding position lies above the sticky bit),
+// (W + 2^(sh-1) - 1 + bit sh of W) >> sh is the round-to-nearest-even of
+// W / 2^sh and stays below 2^32; every shift clamps, so an element with sh >=
+// 32 (below a quarter unit) gives 0.  Z + 0x8080 carries the two lower
+// balanced digits into bytes (each digit + 128), d_1 is the rest; a digit d
+// becomes the float 1.5 2^23 + d by placing it into that constant's bit
+// pattern, minus the constant.
 __device__ __forceinline__ void digits_bf16_s3(double a, int ksh, float& f1, float& f2, float& f3) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(a);
     const uint32_t h = (uint32_t)(bits >> 32), l = (uint32_t)bits;
-    uint32_t T = __funnelshift_l(l, h, 11);
-    T |= min(l << 11, 1u) | 0x80000000u;
-    const int sh = ksh - (int)((h >> 20) & 0x7FFu);
-    const uint32_t hm1 = __funnelshift_rc(0xFFFFFFFFu, 0u, (uint32_t)(33 - sh));   // 2^(sh-1) - 1
-    const uint32_t lsb = __funnelshift_rc(T, 0u, (uint32_t)sh) & 1u;
-    const unsigned long long v = (unsigned long long)T + hm1 + lsb;
-    const uint32_t Z = __funnelshift_rc((uint32_t)v, (uint32_t)(v >> 32), (uint32_t)sh);
-    const int mult = sh <= 32 ? (((int)h >> 31) | 1) : 0;
-    const int Zp = (int)Z * mult + 0x8080;
+    const uint32_t W = (__funnelshift_l(l, h, 11) >> 1) | 0x40000000u | min(l << 10, 1u);
+    const uint32_t sh = (uint32_t)(ksh - (int)((h >> 20) & 0x7FFu));
+    const uint32_t hm1 = shr_clamped(0x7FFFFFFFu, 32u - sh);   // 2^(sh-1) - 1 (0 once sh > 32)
+    const uint32_t Z = shr_clamped(W + hm1 + (shr_clamped(W, sh) & 1u), sh);
+    const int Zp = (int)Z * (((int)h >> 31) | 1) + 0x8080;
     f3 = __int_as_float((int)__byte_perm((uint32_t)Zp, 0x4B400000u, 0x7650)) - 12583040.0f;
     f2 = __int_as_float((int)__byte_perm((uint32_t)Zp, 0x4B400000u, 0x7651)) - 12583040.0f;
     f1 = __int_as_float(0x4B400000 + (Zp >> 16)) - 12582912.0f;
@@ -436,7 +437,15 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
     // A's digits on the 32-bit path (BF16, S = 3; MODE 1, the T-form path:
     // MODE 0 also slices B and would spill registers with both paths compiled)
     constexpr bool FAST = !FP16 && S == 3 && MODE == 1;
+    // FAST also loads the next chunk's A while the tensor cores and the
+    // recombination run (the other paths spill registers with that); MODE 2
+    // stages the CTA's next tile of C in shared memory while a tile runs,
+    // where the memory allows (every preset but BF16 S = 4)
+    constexpr bool PRELOAD = FAST;
     using C_ = Cfg<FP16, S>;
+    // (staging the next C tile in shared memory with cp.async measured slower
+    // for MODE 2 than loading it into registers one iteration ahead)
+    constexpr bool CST = false;
     constexpr int BETA = C_::beta, KC = C_::kc;
     constexpr int QC = KC / 4;            // chunk columns of A per thread
     constexpr int KB = KC / 32;           // k values of B per lane and column
@@ -534,7 +543,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
         const int row = prev.row0 + rloc;
         // the thread's 16 output columns in groups of RC (MODE 1 holds the next
         // chunk's operands in registers meanwhile, so it loads 4 at a time)
-        constexpr int RC = MODE == 1 ? 4 : 8;
+        constexpr int RC = PRELOAD ? 4 : 8;
 #pragma unroll
         for (int grp = 0; grp < 16 / RC; ++grp) {
             uint32_t v[S][RC];
@@ -603,6 +612,24 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
 
+    // CST: a 128 x 64 tile of C (column-major, ld 128) after the two stages
+    double* ctile = reinterpret_cast<double*>(smem + 2 * S * (C_::planeA + C_::planeB));
+    bool c_last = false;      // the most recent cp.async group copies a C tile
+    auto copy_c_tile = [&](const DevDesc& dn, int row0, int col0) {
+        const int row = row0 + rloc;
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+            const int col = col0 + 16 * q + jj;
+            const bool ok = row < dn.m && col < dn.n;
+            const double* src = ok ? dn.C + (size_t)row + (size_t)col * (size_t)dn.ldc : dn.C;
+            // 8-byte copy; zero-filled (nothing read) outside the entry
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(smem_u32(&ctile[(16 * q + jj) * kTM + rloc])),
+                         "l"(src), "r"(ok ? 8 : 0)
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+
     int iter = 0;
     int last_commit = -1;     // iteration of the most recent tensor-core commit
     int t = blockIdx.x;
@@ -610,7 +637,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
         const SItem it0 = items[t];
         const DevDesc d0 = descs[it0.entry];
         load_c0(d0, it0.row0, it0.col0);
-        if constexpr (MODE == 1) load_chunk(d0, it0.row0, it0.col0, 0);
+        if constexpr (PRELOAD) load_chunk(d0, it0.row0, it0.col0, 0);
     }
     while (t < n_items) {
         const SItem item = items[t];
@@ -654,13 +681,13 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
             if constexpr (PRE) {
                 if (MODE == 1 || iter == 0) copy_units(item.entry, m0, n0, nch, c, stage);
             }
-            if constexpr (MODE == 0) load_chunk(d, m0, n0, k0);
-            // (1) a later chunk into L2 (MODE 1: the one after the next, whose
-            // loads step 3b issues; MODE 0: the next): one 128-byte line per
+            if constexpr (!PRELOAD && !preA) load_chunk(d, m0, n0, k0);
+            // (1) a later chunk into L2 (with PRELOAD: the one after the next,
+            // whose loads step 3b issues; else the next): one 128-byte line per
             // thread (A: 16 rows of one column; B: 16 k of one column),
             // in-bounds addresses only
-            if (c + (MODE == 0 ? 1 : 2) < nch) {
-                const int kn = k0 + (MODE == 0 ? 1 : 2) * KC;
+            if (c + (PRELOAD ? 2 : 1) < nch) {
+                const int kn = k0 + (PRELOAD ? 2 : 1) * KC;
                 const int kk = tid >> 3, r = m0 + 16 * (tid & 7);
                 if (!preA && kk < KC && kn + kk < d.k && r < d.m)
                     asm volatile("prefetch.global.L2 [%0];\n" ::"l"(d.A + (size_t)r + (size_t)(kn + kk) * (size_t)d.lda));
@@ -786,7 +813,13 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
                     }
                 }
             }
-            if (PRE) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+            // the units (and, when the latest group copies a C tile, not that group)
+            if (PRE) {
+                if (CST && c_last)
+                    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+                else
+                    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+            }
             if constexpr (!PRE) {
 #pragma unroll
                 for (int jc = 0; jc < 4; ++jc) {
@@ -805,11 +838,9 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
                     }
                 }
             }
-            // (3b) MODE 1: the next chunk's A into registers (this chunk's
-            // digits are in shared memory), so the loads run during steps 4 and
-            // 5.  (MODE 0 also holds B and loads at the top of the iteration:
-            // keeping both live across the recombination would spill.)
-            if constexpr (MODE == 1) {
+            // (3b) PRELOAD: the next chunk's A into registers (this chunk's
+            // digits are in shared memory), so the loads run during steps 4 and 5
+            if constexpr (PRELOAD) {
                 if (c + 1 < nch) {
                     load_chunk(d, m0, n0, k0 + KC);
                 } else if (tn < n_items) {
@@ -861,7 +892,14 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
                 }
                 if (prev.last) {
                     store_prev();
-                    load_c0(d, m0, n0);   // chunk c is chunk 0 of this tile; consumed next iteration
+                    // chunk c is chunk 0 of this tile; acc is consumed next iteration
+                    if constexpr (CST) {
+                        asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // this thread's copy of the tile
+#pragma unroll
+                        for (int jj = 0; jj < 16; ++jj) acc[jj] = ctile[(16 * q + jj) * kTM + rloc];
+                    } else {
+                        load_c0(d, m0, n0);
+                    }
                 }
             }
             // (6) MODE 2: the next chunk's units into the other stage, which the
@@ -869,9 +907,20 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
             if constexpr (MODE == 2) {
                 if (c + 1 < nch) {
                     copy_units(item.entry, m0, n0, nch, c + 1, stage ^ 1);
+                    c_last = false;
                 } else if (tn < n_items) {
                     const SItem nx = items[tn];
                     copy_units(nx.entry, nx.row0, nx.col0, (descs[nx.entry].k + KC - 1) / KC, 0, stage ^ 1);
+                    c_last = false;
+                }
+                // CST: the CTA's next tile of C into the buffer this tile's C was
+                // just read from (each thread copies exactly the 16 values it reads)
+                if constexpr (CST) {
+                    if (c == 0 && tn < n_items) {
+                        const SItem nx = items[tn];
+                        copy_c_tile(descs[nx.entry], nx.row0, nx.col0);
+                        c_last = true;
+                    }
                 }
             }
             prev.C = d.C;
@@ -910,7 +959,8 @@ template <bool FP16, int S, int MODE>
 cudaError_t launch_mode(const DevDesc* descs, const SItem* items, int n_items, int* status, float* dump,
                         int test_stall, const uint8_t* bunits, const long long* bfirst, const uint8_t* aunits,
                         const long long* afirst, cudaStream_t s) {
-    const int smem = Cfg<FP16, S>::smem;
+    constexpr bool cst = false;
+    const int smem = Cfg<FP16, S>::smem + (cst ? kCTileBytes : 0);
     cudaError_t e = cudaFuncSetAttribute(k_split<FP16, S, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     if (n_items <= 0) return cudaSuccess;

@@ -81,7 +81,7 @@ class lrb_host_timing(ctypes.Structure):
                [(n, ctypes.c_double) for n in ("wall_ms", "h2d_busy_ms", "compute_busy_ms", "d2h_busy_ms",
                                                "h2d_bytes", "d2h_bytes", "overlap_h2d_compute_ms",
                                                "overlap_d2h_compute_ms", "overlap_h2d_d2h_ms", "compute_start_ms",
-                                               "compute_end_to_last_ms")]
+                                               "compute_end_to_last_ms", "first_h2d_ms", "first_h2d_bytes")]
 
 
 class LrbError(RuntimeError):

@@ -303,8 +303,12 @@ def test_execute_host_shared_pool():
         h.execute_host(d)
         t = h.host_timing()
         c_elems = int(np.sum(b.m.astype(np.int64) * b.n))
-        assert t["d2h_bytes"] == 8 * c_elems
-        assert t["h2d_bytes"] <= 8 * ((hi - lo) + c_elems)          # the pool once, not per entry
+        c_span = int((b.offC + b.ldc.astype(np.int64) * b.n).max() - b.offC.min())
+        # the C blocks (and the < 256-byte alignment gaps between them) each way,
+        # the pool's span once rather than once per entry
+        assert 8 * c_elems <= t["d2h_bytes"] <= 8 * c_span
+        assert t["h2d_bytes"] <= 8 * ((hi - lo) + c_span)
+        assert t["pieces"] >= 1
         exp1 = oracle_batch(Ah, Ah, C0, b)
         check_entries(C.numpy().copy(), exp1, Ah, Ah, C0, b)
         h.execute_host(d)
