@@ -54,8 +54,6 @@ constexpr int kTM = 128;       // tile rows (MMA M)
 constexpr int kTN = 64;        // tile cols (MMA N)
 constexpr int kThreadsS = 512;
 constexpr int kTmemCols = 512; // 2 sets x S levels x 64 columns
-constexpr int kCTileBytes = 128 * 64 * 8;   // one staged C tile (MODE 2)
-constexpr int kSmemLimit = 227 * 1024;      // dynamic shared memory per CTA
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on any device-side wait
 
 struct SItem {
@@ -438,14 +436,9 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
     // MODE 0 also slices B and would spill registers with both paths compiled)
     constexpr bool FAST = !FP16 && S == 3 && MODE == 1;
     // FAST also loads the next chunk's A while the tensor cores and the
-    // recombination run (the other paths spill registers with that); MODE 2
-    // stages the CTA's next tile of C in shared memory while a tile runs,
-    // where the memory allows (every preset but BF16 S = 4)
+    // recombination run (the other paths spill registers with that)
     constexpr bool PRELOAD = FAST;
     using C_ = Cfg<FP16, S>;
-    // (staging the next C tile in shared memory with cp.async measured slower
-    // for MODE 2 than loading it into registers one iteration ahead)
-    constexpr bool CST = false;
     constexpr int BETA = C_::beta, KC = C_::kc;
     constexpr int QC = KC / 4;            // chunk columns of A per thread
     constexpr int KB = KC / 32;           // k values of B per lane and column
@@ -490,12 +483,19 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
     bool have_prev = false;
     double acc[16];
 
+    // C of the thread's row and 16 columns: the column pointer advances by
+    // ldc; a tile that covers all 16 columns (the usual case) skips the
+    // per-column test
     auto load_c0 = [&](const DevDesc& d, int row0, int col0) {
-        const int row = row0 + rloc;
+        const int row = row0 + rloc, c1 = col0 + 16 * q;
+        const double* cp = d.C + (size_t)row + (size_t)c1 * (size_t)d.ldc;
+        const size_t ld = (size_t)d.ldc;
+        if (row < d.m && c1 + 16 <= d.n) {
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-            const int col = col0 + 16 * q + jj;
-            acc[jj] = (row < d.m && col < d.n) ? d.C[(size_t)row + (size_t)col * (size_t)d.ldc] : 0.0;
+            for (int jj = 0; jj < 16; ++jj) acc[jj] = cp[jj * ld];
+        } else {
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) acc[jj] = (row < d.m && c1 + jj < d.n) ? cp[jj * ld] : 0.0;
         }
     };
 
@@ -562,20 +562,38 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
                 }
             }
             asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            if (dump != nullptr) {   // the diagnostic (a uniform branch, outside the per-output work)
+#pragma unroll
+                for (int jj = 0; jj < RC; ++jj) {
+                    const int j = 16 * q + RC * grp + jj;
+                    if (row < prev.m && prev.col0 + j < prev.n) {
+#pragma unroll
+                        for (int l = 0; l < S; ++l)
+                            dump[(((size_t)prev.c * S + l) * prev.m + row) * prev.n + (prev.col0 + j)] =
+                                __uint_as_float(v[l][jj]);
+                    }
+                }
+            }
+            // the group's column exponents (E + F_j - beta (S + 1) per column)
+            int Fx[RC];
+#pragma unroll
+            for (int jj = 0; jj < RC; jj += 4) {
+                const int4 f4 = *reinterpret_cast<const int4*>(&s_F[prev.stage][16 * q + RC * grp + jj]);
+                Fx[jj] = f4.x;
+                Fx[jj + 1] = f4.y;
+                Fx[jj + 2] = f4.z;
+                Fx[jj + 3] = f4.w;
+            }
 #pragma unroll
             for (int jj = 0; jj < RC; ++jj) {
-                const int j = 16 * q + RC * grp + jj;
                 // level L = l + 2 has weight 2^(beta (S - 1 - l))
                 const long long I = level_integer<FP16, S, RC>(v, jj);
-                if (dump != nullptr && row < prev.m && prev.col0 + j < prev.n) {
-#pragma unroll
-                    for (int l = 0; l < S; ++l)
-                        dump[(((size_t)prev.c * S + l) * prev.m + row) * prev.n + (prev.col0 + j)] =
-                            __uint_as_float(v[l][jj]);
-                }
                 // the exact binary64 value I 2^X (built from bits with integer
-                // instructions), then one binary64 add
-                acc[RC * grp + jj] += scaled_int_to_double(I, E + s_F[prev.stage][j] - BETA * (S + 1));
+                // instructions), then one binary64 add.  (Forming it on the FP64
+                // pipe instead -- 1.5 2^52 + I from bits, minus 1.5 2^52, one FMA
+                // by 2^X -- measured slower: the FP64 pipe, not the integer ALU,
+                // then limits.)
+                acc[RC * grp + jj] += scaled_int_to_double(I, E + Fx[jj] - BETA * (S + 1));
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -583,12 +601,17 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
     };
 
     auto store_prev = [&]() {
-        const int row = prev.row0 + rloc;
+        const int row = prev.row0 + rloc, c1 = prev.col0 + 16 * q;
+        double* cp = prev.C + (size_t)row + (size_t)c1 * (size_t)prev.ldc;
+        const size_t ld = (size_t)prev.ldc;
         if (row < prev.m) {
+            if (c1 + 16 <= prev.n) {
 #pragma unroll
-            for (int jj = 0; jj < 16; ++jj) {
-                const int col = prev.col0 + 16 * q + jj;
-                if (col < prev.n) prev.C[(size_t)row + (size_t)col * (size_t)prev.ldc] = acc[jj];
+                for (int jj = 0; jj < 16; ++jj) cp[jj * ld] = acc[jj];
+            } else {
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj)
+                    if (c1 + jj < prev.n) cp[jj * ld] = acc[jj];
             }
         }
     };
@@ -608,24 +631,6 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
             const uint8_t* src = bunits + (size_t)(bfirst[entry] + (long long)(c0 / kTN) * nch_e + cc) * C_::unitB;
             for (int o = 16 * tid; o < S * C_::planeB; o += 16 * kThreadsS) cp_async16(pb + o, src + o);
             if (tid < kTN / 4) cp_async16(&s_F[stg][4 * tid], src + S * C_::planeB + 16 * tid);
-        }
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-    };
-
-    // CST: a 128 x 64 tile of C (column-major, ld 128) after the two stages
-    double* ctile = reinterpret_cast<double*>(smem + 2 * S * (C_::planeA + C_::planeB));
-    bool c_last = false;      // the most recent cp.async group copies a C tile
-    auto copy_c_tile = [&](const DevDesc& dn, int row0, int col0) {
-        const int row = row0 + rloc;
-#pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-            const int col = col0 + 16 * q + jj;
-            const bool ok = row < dn.m && col < dn.n;
-            const double* src = ok ? dn.C + (size_t)row + (size_t)col * (size_t)dn.ldc : dn.C;
-            // 8-byte copy; zero-filled (nothing read) outside the entry
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(smem_u32(&ctile[(16 * q + jj) * kTM + rloc])),
-                         "l"(src), "r"(ok ? 8 : 0)
-                         : "memory");
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
@@ -699,6 +704,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
             }
             // (2) exponents: A's row maxima over the four quarters through shared
             // memory, B's column maxima by warp shuffles
+            bool tiny_q = false;
             if constexpr (!preA) {
                 if constexpr (FAST) {
                     uint32_t mx = 0, lo = 0;
@@ -709,6 +715,10 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
                         lo |= (uint32_t)b;
                     }
                     s_rkey[q][rloc] = mx | (lo != 0u ? 1u : 0u);
+                    // this quarter alone looks like a row of values below 2^-997
+                    // (a conservative test: another quarter may hold the row's
+                    // large maximum); decided together with the exchange barrier
+                    tiny_q = !key_fast(mx | (lo != 0u ? 1u : 0u));
                 } else {
                     unsigned long long mx = 0;
 #pragma unroll
@@ -737,15 +747,18 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
                     if (lane == 0) s_F[stage][4 * warp + jc] = mx ? exp_of_bits(mx) : 0;
                 }
             }
-            if (!(preA && PRE)) __syncthreads();   // row / column exponents exchanged
-            int E = 0, ksh = 0;
+            // row / column exponents exchanged; FAST: any quarter of tiny values
+            // anywhere (CTA-uniform) sends this chunk down the exact 64-bit path
             bool slow = !FAST;
+            if constexpr (FAST) {
+                slow = __syncthreads_or(tiny_q) != 0;
+            } else {
+                if (!(preA && PRE)) __syncthreads();
+            }
+            int E = 0, ksh = 0;
             if constexpr (!preA) {
                 if constexpr (FAST) {
                     const uint32_t key = max(max(s_rkey[0][rloc], s_rkey[1][rloc]), max(s_rkey[2][rloc], s_rkey[3][rloc]));
-                    // rows of values below 2^-997 (CTA-uniform decision): the
-                    // exact 64-bit maxima and digits for this chunk
-                    slow = __syncthreads_or(!key_fast(key)) != 0;
                     if (!slow) {
                         E = key_exponent(key);
                         ksh = key_shift(key);
@@ -813,13 +826,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
                     }
                 }
             }
-            // the units (and, when the latest group copies a C tile, not that group)
-            if (PRE) {
-                if (CST && c_last)
-                    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-                else
-                    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-            }
+            if (PRE) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
             if constexpr (!PRE) {
 #pragma unroll
                 for (int jc = 0; jc < 4; ++jc) {
@@ -892,14 +899,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
                 }
                 if (prev.last) {
                     store_prev();
-                    // chunk c is chunk 0 of this tile; acc is consumed next iteration
-                    if constexpr (CST) {
-                        asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // this thread's copy of the tile
-#pragma unroll
-                        for (int jj = 0; jj < 16; ++jj) acc[jj] = ctile[(16 * q + jj) * kTM + rloc];
-                    } else {
-                        load_c0(d, m0, n0);
-                    }
+                    load_c0(d, m0, n0);   // chunk c is chunk 0 of this tile; consumed next iteration
                 }
             }
             // (6) MODE 2: the next chunk's units into the other stage, which the
@@ -907,20 +907,9 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
             if constexpr (MODE == 2) {
                 if (c + 1 < nch) {
                     copy_units(item.entry, m0, n0, nch, c + 1, stage ^ 1);
-                    c_last = false;
                 } else if (tn < n_items) {
                     const SItem nx = items[tn];
                     copy_units(nx.entry, nx.row0, nx.col0, (descs[nx.entry].k + KC - 1) / KC, 0, stage ^ 1);
-                    c_last = false;
-                }
-                // CST: the CTA's next tile of C into the buffer this tile's C was
-                // just read from (each thread copies exactly the 16 values it reads)
-                if constexpr (CST) {
-                    if (c == 0 && tn < n_items) {
-                        const SItem nx = items[tn];
-                        copy_c_tile(descs[nx.entry], nx.row0, nx.col0);
-                        c_last = true;
-                    }
                 }
             }
             prev.C = d.C;
@@ -959,8 +948,7 @@ template <bool FP16, int S, int MODE>
 cudaError_t launch_mode(const DevDesc* descs, const SItem* items, int n_items, int* status, float* dump,
                         int test_stall, const uint8_t* bunits, const long long* bfirst, const uint8_t* aunits,
                         const long long* afirst, cudaStream_t s) {
-    constexpr bool cst = false;
-    const int smem = Cfg<FP16, S>::smem + (cst ? kCTileBytes : 0);
+    const int smem = Cfg<FP16, S>::smem;
     cudaError_t e = cudaFuncSetAttribute(k_split<FP16, S, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     if (n_items <= 0) return cudaSuccess;
