@@ -54,10 +54,32 @@ def wide(batch):
     return batch
 
 
+def plant_special_rows(b, p):
+    """Rows of A that exercise every branch of the digit extraction: a zero
+    row, rows of values below 2^-997 in one chunk only (the exact 64-bit path;
+    one subnormal), exact half-unit ties of the rounding, and a row maximum
+    just below a power of two (its top digit rounds up to 2^beta)."""
+    A = entry_view(b.A.numpy(), int(b.offA[0]), int(b.m[0]), int(b.k[0]), int(b.lda[0]))
+    kc = p.kc
+    A[3, :] = 0.0
+    A[5, kc:2 * kc] = np.random.default_rng(1).standard_normal(kc) * 1e-305
+    A[5, kc + 7] = 5e-324
+    E = 3                                   # ties: (Z + 1/2) 2^(E - beta S) with |values| < 2^E
+    Z = np.arange(1, 40) * 977
+    A[9, :len(Z)] = np.ldexp(Z + 0.5, E - p.beta * p.S)
+    A[9, 50] = np.ldexp(1.0, E) * (1 - 2.0 ** -40)
+    A[11, :] = np.ldexp(1.0 - 2.0 ** -53, 2) * np.sign(np.random.default_rng(2).standard_normal(A.shape[1]))
+    return b
+
+
 @pytest.mark.parametrize("name", sorted(PREC))
-def test_level_sums_bitwise(handle, name):
+@pytest.mark.parametrize("n", [70, 40])
+def test_level_sums_bitwise(handle, name, n):
+    # n = 70: several column tiles, both operands sliced by the pre-passes;
+    # n = 40: one column tile, A sliced inside the kernel (the 32-bit digit
+    # path for BF16 S = 3, with the special rows below)
     p = PRESETS[name]
-    b = wide(ragged_batch([(150, 70, 2 * p.kc + 44)], pad=2, seed=7))
+    b = plant_special_rows(wide(ragged_batch([(150, n, 2 * p.kc + 44)], pad=2, seed=7)), p)
     Ah, Bh, C0 = host(b.A), host(b.B), host(b.C)
     A, B, _ = mats(b, 0, Ah, Bh, C0)
     m, n, k = A.shape[0], B.shape[1], A.shape[1]
