@@ -109,11 +109,11 @@ namespace {
 // Build and launch one wave on slot s (called without the queue lock).
 lrb_status launch_split_wave(lrb_queue* q, Slot& s, const std::vector<lrb_gemm_desc>& all, int precision) {
     (void)q;
-    std::vector<int4> items;
+    std::vector<split::STile> items;
     split::build_items(all.data(), all.size(), items);
     auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t o_items = align(sizeof(DevDesc) * all.size());
-    const size_t o_status = o_items + align(sizeof(int4) * std::max<size_t>(items.size(), 1));
+    const size_t o_items = 0;
+    const size_t o_status = o_items + align(sizeof(split::STile) * std::max<size_t>(items.size(), 1));
     const size_t need = o_status + 256;
     if (need > s.dmem_bytes) {
         if (s.dmem) cudaFreeAsync(s.dmem, s.stream);
@@ -125,14 +125,12 @@ lrb_status launch_split_wave(lrb_queue* q, Slot& s, const std::vector<lrb_gemm_d
     }
     char* base = (char*)s.dmem;
     int* d_status = (int*)(base + o_status);
-    cudaError_t e = cudaMemcpyAsync(base, all.data(), sizeof(DevDesc) * all.size(), cudaMemcpyHostToDevice, s.stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(base + o_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice,
-                            s.stream);
+    cudaError_t e = cudaMemcpyAsync(base + o_items, items.data(), sizeof(split::STile) * items.size(),
+                                    cudaMemcpyHostToDevice, s.stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, sizeof(int), s.stream);
     if (e == cudaSuccess)
-        e = split::launch_raw(precision, (const DevDesc*)base, (const int4*)(base + o_items), (int)items.size(),
-                              d_status, s.stream);
+        e = split::launch_raw(precision, (const split::STile*)(base + o_items), (int)items.size(), d_status,
+                              s.stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s.h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost, s.stream);
     if (e == cudaSuccess) e = cudaEventRecord(s.done, s.stream);
     return e == cudaSuccess ? LRB_OK : LRB_ERR_DEVICE;

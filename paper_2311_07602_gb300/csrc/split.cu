@@ -56,9 +56,6 @@ constexpr int kThreadsS = 512;
 constexpr int kTmemCols = 512; // 2 sets x S levels x 64 columns
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on any device-side wait
 
-struct SItem {
-    int32_t entry, row0, col0, pad;
-};
 
 template <bool FP16, int S>
 struct Cfg {
@@ -419,8 +416,7 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* src) {
 // (w = warp, = its TMEM lane), quarter q = w / 4 of the chunk's columns for
 // slicing and of the tile's 64 output columns for recombination.
 template <bool FP16, int S, int MODE>
-__global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restrict__ descs,
-                                                         const SItem* __restrict__ items, int n_items,
+__global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict__ tiles, int n_items,
                                                          int* __restrict__ status, float* __restrict__ dump,
                                                          int test_stall, const uint8_t* __restrict__ bunits,
                                                          const long long* __restrict__ bfirst,
@@ -449,6 +445,10 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
     __shared__ __align__(16) int s_F[2][kTN];
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ __align__(8) uint64_t s_never;   // test_stall: a barrier nothing arrives on
+    // the records of the CTA's current tile and its next two (a ring: the
+    // record two tiles ahead is copied while a tile starts, so no tile waits
+    // on a global load of its own record)
+    __shared__ __align__(16) STile s_tile[3];
     __shared__ uint32_t s_tmem;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -638,25 +638,40 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
     int iter = 0;
     int last_commit = -1;     // iteration of the most recent tensor-core commit
     int t = blockIdx.x;
-    if (t < n_items) {
-        const SItem it0 = items[t];
-        const DevDesc d0 = descs[it0.entry];
-        load_c0(d0, it0.row0, it0.col0);
-        if constexpr (PRELOAD) load_chunk(d0, it0.row0, it0.col0, 0);
+    if (tid < 8) {   // the first two records, synchronously
+        const int tt = t + (tid >> 2) * (int)gridDim.x;
+        if (tt < n_items)
+            reinterpret_cast<uint4*>(&s_tile[tid >> 2])[tid & 3] = reinterpret_cast<const uint4*>(tiles + tt)[tid & 3];
     }
+    __syncthreads();
+    if (t < n_items) {
+        const STile& r0 = s_tile[0];
+        load_c0(r0.d, r0.row0, r0.col0);
+        if constexpr (PRELOAD) load_chunk(r0.d, r0.row0, r0.col0, 0);
+    }
+    int ti = 0;   // index of the CTA's current tile (its record is s_tile[ti % 3])
     while (t < n_items) {
-        const SItem item = items[t];
-        const DevDesc d = descs[item.entry];
-        const int m0 = item.row0, n0 = item.col0;
+        const STile& cur = s_tile[ti % 3];
+        const DevDesc d = cur.d;
+        const int entry = cur.entry;
+        const int m0 = cur.row0, n0 = cur.col0;
         const int nch = (d.k + KC - 1) / KC;
         const int tn = t + gridDim.x;
+        const STile& nxt = s_tile[(ti + 1) % 3];   // valid when tn < n_items
         {
+            // the record two tiles ahead into the ring slot the previous tile
+            // used (one commit group; waited for before this chunk's tensor-core
+            // issue and visible to every thread after the barrier there)
+            const int t2 = tn + gridDim.x;
+            if (tid < 4 && t2 < n_items) cp_async16(reinterpret_cast<uint4*>(&s_tile[(ti + 2) % 3]) + tid,
+                                                    reinterpret_cast<const uint4*>(tiles + t2) + tid);
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
             // the CTA's next tile into L2 while this one runs: its C (one
             // 128-byte line of 16 rows per thread) and, when pre-sliced, its
             // first chunk's digit units
             if (tn < n_items) {
-                const SItem nx = items[tn];
-                const DevDesc dn = descs[nx.entry];
+                const STile& nx = nxt;
+                const DevDesc dn = nx.d;
                 const int jj = tid >> 3, r = nx.row0 + 16 * (tid & 7);
                 if (jj < kTN && nx.col0 + jj < dn.n && r < dn.m)
                     asm volatile("prefetch.global.L2 [%0];\n" ::"l"(dn.C + (size_t)r + (size_t)(nx.col0 + jj) * (size_t)dn.ldc));
@@ -684,7 +699,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
             // copies the next chunk's units one iteration ahead (step 6), so
             // only the CTA's first chunk copies its own here.
             if constexpr (PRE) {
-                if (MODE == 1 || iter == 0) copy_units(item.entry, m0, n0, nch, c, stage);
+                if (MODE == 1 || iter == 0) copy_units(entry, m0, n0, nch, c, stage);
             }
             if constexpr (!PRELOAD && !preA) load_chunk(d, m0, n0, k0);
             // (1) a later chunk into L2 (with PRELOAD: the one after the next,
@@ -826,7 +841,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
                     }
                 }
             }
-            if (PRE) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // units and the tile record
             if constexpr (!PRE) {
 #pragma unroll
                 for (int jc = 0; jc < 4; ++jc) {
@@ -851,8 +866,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
                 if (c + 1 < nch) {
                     load_chunk(d, m0, n0, k0 + KC);
                 } else if (tn < n_items) {
-                    const SItem nx = items[tn];
-                    load_chunk(descs[nx.entry], nx.row0, nx.col0, 0);
+                    load_chunk(nxt.d, nxt.row0, nxt.col0, 0);
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -906,10 +920,9 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
             // recombination just finished with (and the MMAs that read it are done)
             if constexpr (MODE == 2) {
                 if (c + 1 < nch) {
-                    copy_units(item.entry, m0, n0, nch, c + 1, stage ^ 1);
+                    copy_units(entry, m0, n0, nch, c + 1, stage ^ 1);
                 } else if (tn < n_items) {
-                    const SItem nx = items[tn];
-                    copy_units(nx.entry, nx.row0, nx.col0, (descs[nx.entry].k + KC - 1) / KC, 0, stage ^ 1);
+                    copy_units(nxt.entry, nxt.row0, nxt.col0, (nxt.d.k + KC - 1) / KC, 0, stage ^ 1);
                 }
             }
             prev.C = d.C;
@@ -925,6 +938,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
         }
         if (failed) break;
         t = tn;
+        ++ti;
     }
     if (have_prev && !failed) {
         const bool ok = recombine((uint32_t)(((iter - 1) >> 1) & 1));
@@ -945,7 +959,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const DevDesc* __restric
 }
 
 template <bool FP16, int S, int MODE>
-cudaError_t launch_mode(const DevDesc* descs, const SItem* items, int n_items, int* status, float* dump,
+cudaError_t launch_mode(const STile* items, int n_items, int* status, float* dump,
                         int test_stall, const uint8_t* bunits, const long long* bfirst, const uint8_t* aunits,
                         const long long* afirst, cudaStream_t s) {
     const int smem = Cfg<FP16, S>::smem;
@@ -956,7 +970,7 @@ cudaError_t launch_mode(const DevDesc* descs, const SItem* items, int n_items, i
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = std::max(1, std::min(n_items, sms));
-    k_split<FP16, S, MODE><<<grid, kThreadsS, smem, s>>>(descs, items, n_items, status, dump, test_stall, bunits,
+    k_split<FP16, S, MODE><<<grid, kThreadsS, smem, s>>>(items, n_items, status, dump, test_stall, bunits,
                                                          bfirst, aunits, afirst);
     return cudaGetLastError();
 }
@@ -964,17 +978,16 @@ cudaError_t launch_mode(const DevDesc* descs, const SItem* items, int n_items, i
 // Items [0, n_b) take mode 1 (or 0 without pre-sliced B), items [n_b, n_items)
 // mode 2 (their entries have pre-sliced A): two launches in stream order.
 template <bool FP16, int S>
-cudaError_t launch_t(const DevDesc* descs, const SItem* items, int n_items, int n_b, int* status, float* dump,
-                     int test_stall, const uint8_t* bunits, const long long* bfirst, const uint8_t* aunits,
-                     const long long* afirst, cudaStream_t s) {
+cudaError_t launch_t(const STile* items, int n_items, int n_b, int* status, float* dump, int test_stall,
+                     const uint8_t* bunits, const long long* bfirst, const uint8_t* aunits, const long long* afirst,
+                     cudaStream_t s) {
     if (bunits == nullptr)
-        return launch_mode<FP16, S, 0>(descs, items, n_items, status, dump, test_stall, nullptr, nullptr, nullptr,
-                                       nullptr, s);
-    cudaError_t e = launch_mode<FP16, S, 1>(descs, items, n_b, status, dump, test_stall, bunits, bfirst, nullptr,
-                                            nullptr, s);
+        return launch_mode<FP16, S, 0>(items, n_items, status, dump, test_stall, nullptr, nullptr, nullptr, nullptr,
+                                       s);
+    cudaError_t e = launch_mode<FP16, S, 1>(items, n_b, status, dump, test_stall, bunits, bfirst, nullptr, nullptr, s);
     if (e == cudaSuccess && n_items > n_b)
-        e = launch_mode<FP16, S, 2>(descs, items + n_b, n_items - n_b, status, dump, test_stall, bunits, bfirst,
-                                    aunits, afirst, s);
+        e = launch_mode<FP16, S, 2>(items + n_b, n_items - n_b, status, dump, test_stall, bunits, bfirst, aunits,
+                                    afirst, s);
     return e;
 }
 
@@ -1009,22 +1022,18 @@ size_t unit_bytes(int precision, bool a_side) {
     }
 }
 
-cudaError_t launch_prec(int precision, const DevDesc* descs, const SItem* items, int n_items, int n_b, int* status,
-                        float* dump, int test_stall, const uint8_t* bunits, const long long* bfirst,
-                        const uint8_t* aunits, const long long* afirst, cudaStream_t s) {
+cudaError_t launch_prec(int precision, const STile* items, int n_items, int n_b, int* status, float* dump,
+                        int test_stall, const uint8_t* bunits, const long long* bfirst, const uint8_t* aunits,
+                        const long long* afirst, cudaStream_t s) {
     switch (precision) {
         case LRB_PREC_SPLIT_BF16_S3:
-            return launch_t<false, 3>(descs, items, n_items, n_b, status, dump, test_stall, bunits, bfirst, aunits,
-                                      afirst, s);
+            return launch_t<false, 3>(items, n_items, n_b, status, dump, test_stall, bunits, bfirst, aunits, afirst, s);
         case LRB_PREC_SPLIT_BF16_S4:
-            return launch_t<false, 4>(descs, items, n_items, n_b, status, dump, test_stall, bunits, bfirst, aunits,
-                                      afirst, s);
+            return launch_t<false, 4>(items, n_items, n_b, status, dump, test_stall, bunits, bfirst, aunits, afirst, s);
         case LRB_PREC_SPLIT_FP16_S3:
-            return launch_t<true, 3>(descs, items, n_items, n_b, status, dump, test_stall, bunits, bfirst, aunits,
-                                     afirst, s);
+            return launch_t<true, 3>(items, n_items, n_b, status, dump, test_stall, bunits, bfirst, aunits, afirst, s);
         case LRB_PREC_SPLIT_FP16_S4:
-            return launch_t<true, 4>(descs, items, n_items, n_b, status, dump, test_stall, bunits, bfirst, aunits,
-                                     afirst, s);
+            return launch_t<true, 4>(items, n_items, n_b, status, dump, test_stall, bunits, bfirst, aunits, afirst, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1036,7 +1045,7 @@ struct SplitPlan {
     int test_stall = 0;
     void* dmem = nullptr;
     DevDesc* d_descs = nullptr;
-    SItem* d_items = nullptr;
+    STile* d_items = nullptr;
     int* d_status = nullptr;
     int n_items = 0;
     // pre-sliced B (nullptr: the kernel slices B itself) and A (entries with
@@ -1052,18 +1061,26 @@ struct SplitPlan {
     int n_items_b = 0;   // items [0, n_items_b) have A sliced in the kernel, the rest pre-sliced
 };
 
-void build_items(const lrb_gemm_desc* descs, size_t count, std::vector<int4>& items) {
+STile make_tile(const lrb_gemm_desc& d, size_t entry, int row0, int col0) {
+    STile t;
+    std::memcpy(&t.d, &d, sizeof(DevDesc));
+    t.entry = (int32_t)entry;
+    t.row0 = row0;
+    t.col0 = col0;
+    t.pad = 0;
+    return t;
+}
+
+void build_items(const lrb_gemm_desc* descs, size_t count, std::vector<STile>& items) {
     items.clear();
     for (size_t e = 0; e < count; ++e)
         for (int c0 = 0; c0 < descs[e].n; c0 += kTN)
-            for (int r0 = 0; r0 < descs[e].m; r0 += kTM) items.push_back(make_int4((int)e, r0, c0, 0));
+            for (int r0 = 0; r0 < descs[e].m; r0 += kTM) items.push_back(make_tile(descs[e], e, r0, c0));
 }
 
-cudaError_t launch_raw(int precision, const DevDesc* d_descs, const int4* d_items, int n_items, int* d_status,
-                       cudaStream_t s) {
-    static_assert(sizeof(int4) == sizeof(SItem), "tile layout");
-    return launch_prec(precision, d_descs, reinterpret_cast<const SItem*>(d_items), n_items, n_items, d_status,
-                       nullptr, 0, nullptr, nullptr, nullptr, nullptr, s);
+cudaError_t launch_raw(int precision, const STile* d_items, int n_items, int* d_status, cudaStream_t s) {
+    return launch_prec(precision, d_items, n_items, n_items, d_status, nullptr, 0, nullptr, nullptr, nullptr, nullptr,
+                       s);
 }
 
 int chunk_len(int precision) {
@@ -1087,12 +1104,12 @@ lrb_status create(int device, int sms, const lrb_gemm_desc* descs, size_t count,
     *out = nullptr;
     // tiles of entries with one column tile first (their A is sliced in the
     // kernel), then the entries whose A is pre-sliced (several column tiles)
-    std::vector<SItem> items;
+    std::vector<STile> items;
     for (int pass = 0; pass < 2; ++pass)
         for (size_t e = 0; e < count; ++e)
             if (pre_a(descs[e]) == (pass == 1))
                 for (int c0 = 0; c0 < descs[e].n; c0 += kTN)
-                    for (int r0 = 0; r0 < descs[e].m; r0 += kTM) items.push_back(SItem{(int32_t)e, r0, c0, 0});
+                    for (int r0 = 0; r0 < descs[e].m; r0 += kTM) items.push_back(make_tile(descs[e], e, r0, c0));
     size_t n_items_b = 0;
     for (size_t e = 0; e < count; ++e)
         if (!pre_a(descs[e])) n_items_b += (size_t)((descs[e].n + kTN - 1) / kTN) * ((descs[e].m + kTM - 1) / kTM);
@@ -1104,7 +1121,7 @@ lrb_status create(int device, int sms, const lrb_gemm_desc* descs, size_t count,
     p->precision = precision;
     p->test_stall = test_stall;
     const size_t o_items = ((sizeof(DevDesc) * count + 255) / 256) * 256;
-    const size_t o_status = o_items + ((sizeof(SItem) * std::max<size_t>(items.size(), 1) + 255) / 256) * 256;
+    const size_t o_status = o_items + ((sizeof(STile) * std::max<size_t>(items.size(), 1) + 255) / 256) * 256;
     cudaError_t ce = cudaMalloc(&p->dmem, o_status + 256);
     if (ce != cudaSuccess) {
         delete p;
@@ -1112,13 +1129,13 @@ lrb_status create(int device, int sms, const lrb_gemm_desc* descs, size_t count,
         return LRB_ERR_NOMEM;
     }
     p->d_descs = (DevDesc*)p->dmem;
-    p->d_items = (SItem*)((char*)p->dmem + o_items);
+    p->d_items = (STile*)((char*)p->dmem + o_items);
     p->d_status = (int*)((char*)p->dmem + o_status);
     p->n_items = (int)items.size();
     p->n_items_b = (int)n_items_b;
     ce = cudaMemcpy(p->d_descs, descs, sizeof(DevDesc) * count, cudaMemcpyHostToDevice);
     if (ce == cudaSuccess && !items.empty())
-        ce = cudaMemcpy(p->d_items, items.data(), sizeof(SItem) * items.size(), cudaMemcpyHostToDevice);
+        ce = cudaMemcpy(p->d_items, items.data(), sizeof(STile) * items.size(), cudaMemcpyHostToDevice);
     if (ce == cudaSuccess) ce = cudaMemset(p->d_status, 0, 256);
     if (ce != cudaSuccess) {
         cudaFree(p->dmem);
@@ -1197,7 +1214,7 @@ cudaError_t launch_with(SplitPlan* p, float* dump, cudaStream_t s) {
             e = slice_prec(p->precision, true, p->d_descs, p->d_aunits, p->n_aunits, p->aunits, s);
         if (e != cudaSuccess) return e;
     }
-    return launch_prec(p->precision, p->d_descs, p->d_items, p->n_items, p->bunits ? p->n_items_b : p->n_items,
+    return launch_prec(p->precision, p->d_items, p->n_items, p->bunits ? p->n_items_b : p->n_items,
                        p->d_status, dump, p->test_stall, p->bunits, p->d_bfirst, p->aunits, p->d_afirst, s);
 }
 

@@ -21,12 +21,18 @@ cudaError_t launch(SplitPlan* p, cudaStream_t s);
 cudaError_t launch_dump(SplitPlan* p, float* dump, cudaStream_t s);
 // Reads the plan's device status word (1 after a bounded wait expired).
 int read_status(SplitPlan* p, cudaStream_t s, int* value);
-// Tile list (int4 per 128 x 64 output tile: entry, row0, col0, 0) of a batch
-// and the launch of the split kernel on uploaded descriptors / tiles (used by
-// the serving queue, whose waves live in stream-slot memory).
-void build_items(const lrb_gemm_desc* descs, size_t count, std::vector<int4>& items);
-cudaError_t launch_raw(int precision, const DevDesc* d_descs, const int4* d_items, int n_items, int* d_status,
-                       cudaStream_t s);
+// One 128 x 64 output tile of the split kernel with its entry's descriptor
+// (64 bytes, so a tile is described by one record the kernel can prefetch).
+struct STile {
+    DevDesc d;
+    int32_t entry, row0, col0, pad;
+};
+static_assert(sizeof(STile) == 64, "tile record layout");
+
+// Tile list of a batch and the launch of the split kernel on uploaded tiles
+// (used by the serving queue, whose waves live in stream-slot memory).
+void build_items(const lrb_gemm_desc* descs, size_t count, std::vector<STile>& items);
+cudaError_t launch_raw(int precision, const STile* d_items, int n_items, int* d_status, cudaStream_t s);
 int chunk_len(int precision);
 int digit_count(int precision);
 void destroy(SplitPlan* p);
