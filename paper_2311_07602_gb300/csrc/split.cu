@@ -13,9 +13,9 @@
 //     balanced digits, lowest first: d_s = ((Z + 2^(beta-1)) mod 2^beta) -
 //     2^(beta-1), Z = (Z - d_s) / 2^beta for s = S..2, d_1 = Z;
 //   * pairs (s, t) with s + t <= S + 1 are multiplied; pairs of one level
-//     L = s + t accumulate in one FP32 TMEM accumulator, exact because kc
-//     keeps every level sum within 2^24 (BF16: beta 8, kc 64; FP16: beta 9,
-//     kc 32);
+//     L = s + t accumulate in one FP32 TMEM accumulator (BF16 S = 3: level
+//     4's (2, 2) pair in a second one), exact because kc keeps every level
+//     sum within 2^24 (BF16: beta 8, kc 64; FP16: beta 9, kc 32);
 //   * per chunk the level sums are combined exactly as a 64-bit integer
 //     I = sum_L P_L 2^(beta (S+1-L)) (|I| < 2^53), turned into the binary64
 //     value I 2^(E_i + F_j - beta (S+1)) without rounding, and added to a
@@ -53,7 +53,7 @@ namespace {
 constexpr int kTM = 128;       // tile rows (MMA M)
 constexpr int kTN = 64;        // tile cols (MMA N)
 constexpr int kThreadsS = 512;
-constexpr int kTmemCols = 512; // 2 sets x S levels x 64 columns
+constexpr int kTmemCols = 512; // 2 sets x (up to) 4 accumulators x 64 columns
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on any device-side wait
 
 
@@ -238,46 +238,62 @@ __device__ __forceinline__ void digits_bf16_s3(double a, int ksh, float& f1, flo
     f1 = __int_as_float(0x4B400000 + (Zp >> 16)) - 12582912.0f;
 }
 
-// Largest |P_L| one k-chunk can produce for level L (kc times the level's
-// kept pairs' largest digit products; max|d_1| = 2^beta, max|d_s| = 2^(beta-1)).
+// TMEM accumulators per chunk: one per level L = 2 .. S + 1, except that
+// BF16 S = 3 gives the (2, 2) pair of level 4 one of its own.  Level 4 can
+// reach 5 2^20 there, beyond the 2^22 of the conversion below; its parts
+// (1, 3) + (3, 1) and (2, 2) stay within 2^22 and 2^20.
 template <bool FP16, int S>
-__host__ __device__ constexpr long long level_bound_c(int L) {
+__host__ __device__ constexpr int n_acc() { return (!FP16 && S == 3) ? S + 1 : S; }
+
+// The accumulator of digit pair (s, t).
+template <bool FP16, int S>
+__host__ __device__ constexpr int acc_of(int s, int t) {
+    return (!FP16 && S == 3 && s == 2 && t == 2) ? S : s + t - 2;
+}
+
+// Largest |P| one k-chunk can produce in accumulator g (kc times its kept
+// pairs' largest digit products; max|d_1| = 2^beta, max|d_s| = 2^(beta-1)).
+template <bool FP16, int S>
+__host__ __device__ constexpr long long acc_bound_c(int g) {
     const int beta = FP16 ? 9 : 8, kc = FP16 ? 32 : 64;
     long long b = 0;
     for (int s = 1; s <= S; ++s)
         for (int t = 1; t <= S; ++t)
-            if (s + t == L && s + t <= S + 1) b += (long long)(s == 1 ? 1 << beta : 1 << (beta - 1)) * (t == 1 ? 1 << beta : 1 << (beta - 1));
+            if (s + t <= S + 1 && acc_of<FP16, S>(s, t) == g)
+                b += (long long)(s == 1 ? 1 << beta : 1 << (beta - 1)) * (t == 1 ? 1 << beta : 1 << (beta - 1));
     return b * kc;
 }
 
-// Level sum L = l + 2 of an FP32 accumulator as an integer.  Where |P_L| <=
-// 2^22 the float P + 1.5 2^23 is exact and its bit pattern is 0x4B400000 + P
-// (an FP32 add, no conversion instruction); larger bounds convert.
+// Accumulator g as an integer.  Where |P| <= 2^22 the float P + 1.5 2^23 is
+// exact and its bit pattern is 0x4B400000 + P (an FP32 add, no conversion
+// instruction); larger bounds convert.
 template <bool FP16, int S>
-__device__ __forceinline__ int level_value(uint32_t v, int l) {
-    if (level_bound_c<FP16, S>(l + 2) <= (1ll << 22))
+__device__ __forceinline__ int acc_value(uint32_t v, int g) {
+    if (acc_bound_c<FP16, S>(g) <= (1ll << 22))
         return __float_as_int(__uint_as_float(v) + 12582912.0f) - 0x4B400000;
     return __float2int_rn(__uint_as_float(v));
 }
 
-// I = sum_L P_L 2^(beta (S + 1 - L)) of one output (levels L = l + 2 in
-// v[l]).  BF16: the two lowest levels combine in 32 bits (|P_L 2^8 + P_L'| <
-// 2^31), as do the two highest for S = 4, and one wide multiply-add joins them.
+// I = sum_L P_L 2^(beta (S + 1 - L)) of one output (accumulator g in v[g];
+// level L = g + 2 for g < S).  BF16: the two lowest levels combine in 32 bits
+// (|P_L 2^8 + P_L'| < 2^31), as do the two highest for S = 4, and one wide
+// multiply-add joins them.
 template <bool FP16, int S, int RC>
-__device__ __forceinline__ long long level_integer(const uint32_t (&v)[S][RC], int jj) {
+__device__ __forceinline__ long long level_integer(const uint32_t (&v)[n_acc<FP16, S>()][RC], int jj) {
     if constexpr (!FP16 && S == 3) {
-        const int hi = level_value<FP16, S>(v[0][jj], 0);
-        const int lo = level_value<FP16, S>(v[1][jj], 1) * 256 + level_value<FP16, S>(v[2][jj], 2);
+        const int hi = acc_value<FP16, S>(v[0][jj], 0);
+        const int p4 = acc_value<FP16, S>(v[2][jj], 2) + acc_value<FP16, S>(v[3][jj], 3);
+        const int lo = acc_value<FP16, S>(v[1][jj], 1) * 256 + p4;
         return (long long)hi * 65536 + lo;
     } else if constexpr (!FP16 && S == 4) {
-        const int hi = level_value<FP16, S>(v[0][jj], 0) * 256 + level_value<FP16, S>(v[1][jj], 1);
-        const int lo = level_value<FP16, S>(v[2][jj], 2) * 256 + level_value<FP16, S>(v[3][jj], 3);
+        const int hi = acc_value<FP16, S>(v[0][jj], 0) * 256 + acc_value<FP16, S>(v[1][jj], 1);
+        const int lo = acc_value<FP16, S>(v[2][jj], 2) * 256 + acc_value<FP16, S>(v[3][jj], 3);
         return (long long)hi * 65536 + lo;
     } else {
         constexpr int BETA = FP16 ? 9 : 8;
         long long I = 0;
 #pragma unroll
-        for (int l = 0; l < S; ++l) I = I * (1ll << BETA) + level_value<FP16, S>(v[l][jj], l);
+        for (int l = 0; l < S; ++l) I = I * (1ll << BETA) + acc_value<FP16, S>(v[l][jj], l);
         return I;
     }
 }
@@ -438,18 +454,32 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
     constexpr int BETA = C_::beta, KC = C_::kc;
     constexpr int QC = KC / 4;            // chunk columns of A per thread
     constexpr int KB = KC / 32;           // k values of B per lane and column
+    constexpr int NACC = n_acc<FP16, S>();   // TMEM accumulators (64 columns each) per stage
+    static_assert(2 * NACC * kTN <= kTmemCols, "two stages of accumulators must fit the TMEM allocation");
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ unsigned long long s_rmax[4][kTM];
     __shared__ uint32_t s_rkey[4][kTM];
-    __shared__ __align__(16) int s_E[2][kTM];
-    __shared__ __align__(16) int s_F[2][kTN];
+    // row and column exponents of the last three chunks (slot = chunk index
+    // mod 3): a thread may write chunk i + 1's while another still reads chunk
+    // i - 1's in its recombination; one that writes chunk i + 2's has passed
+    // the barrier that every thread reaches only after that recombination
+    __shared__ __align__(16) int s_E[3][kTM];
+    __shared__ __align__(16) int s_F[3][kTN];
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ __align__(8) uint64_t s_never;   // test_stall: a barrier nothing arrives on
-    // the records of the CTA's current tile and its next two (a ring: the
-    // record two tiles ahead is copied while a tile starts, so no tile waits
-    // on a global load of its own record)
-    __shared__ __align__(16) STile s_tile[3];
+    // the records of the CTA's tiles in a ring of four: the record two tiles
+    // ahead is copied while a tile starts, so no tile waits on a global load
+    // of its own record.  Slot ti & 3 holds tile ti.  A thread that starts
+    // tile ti + 1 (and writes slot (ti + 3) & 3) may meet threads still in
+    // tile ti, which read slots ti & 3 and (ti + 1) & 3, never one still in
+    // tile ti - 1.
+    __shared__ __align__(16) STile s_tile[4];
     __shared__ uint32_t s_tmem;
+    // a recombination wait expired in an iteration of this parity: set before
+    // the next iteration's issue barrier, read by every thread after it (a
+    // thread still reading iteration i's slot cannot meet a write to it from
+    // iteration i + 2, which needs that barrier passed)
+    __shared__ int s_fail[2];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int rloc = 32 * (warp & 3) + lane;   // tile row (TMEM lane)
@@ -464,6 +494,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s_bar[0])));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s_bar[1])));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s_never)));
+        s_fail[0] = s_fail[1] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -477,7 +508,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
     struct Prev {
         double* C;          // the tile's entry: C, its extent and leading dimension
         int m, n, ldc;
-        int row0, col0, c, stage;
+        int row0, col0, c, stage, slot;
         bool last;
     } prev{};
     bool have_prev = false;
@@ -539,17 +570,17 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
         if (test_stall && !__all_sync(0xffffffffu, mbar_wait(smem_u32(&s_never), 0))) return false;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-        const int E = s_E[prev.stage][rloc];
+        const int E = s_E[prev.slot][rloc];
         const int row = prev.row0 + rloc;
         // the thread's 16 output columns in groups of RC (MODE 1 holds the next
         // chunk's operands in registers meanwhile, so it loads 4 at a time)
         constexpr int RC = PRELOAD ? 4 : 8;
 #pragma unroll
         for (int grp = 0; grp < 16 / RC; ++grp) {
-            uint32_t v[S][RC];
+            uint32_t v[NACC][RC];
 #pragma unroll
-            for (int l = 0; l < S; ++l) {
-                const uint32_t ta = tmem + lane_base + (uint32_t)(prev.stage * S * kTN + l * kTN + 16 * q + RC * grp);
+            for (int l = 0; l < NACC; ++l) {
+                const uint32_t ta = tmem + lane_base + (uint32_t)(prev.stage * NACC * kTN + l * kTN + 16 * q + RC * grp);
                 if constexpr (RC == 8) {
                     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
                                  : "=r"(v[l][0]), "=r"(v[l][1]), "=r"(v[l][2]), "=r"(v[l][3]), "=r"(v[l][4]),
@@ -568,9 +599,12 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
                     const int j = 16 * q + RC * grp + jj;
                     if (row < prev.m && prev.col0 + j < prev.n) {
 #pragma unroll
-                        for (int l = 0; l < S; ++l)
-                            dump[(((size_t)prev.c * S + l) * prev.m + row) * prev.n + (prev.col0 + j)] =
-                                __uint_as_float(v[l][jj]);
+                        for (int l = 0; l < S; ++l) {
+                            // a level's parts are integers below 2^24 in sum: exact
+                            float val = __uint_as_float(v[l][jj]);
+                            if (NACC > S && l == S - 1) val += __uint_as_float(v[S][jj]);
+                            dump[(((size_t)prev.c * S + l) * prev.m + row) * prev.n + (prev.col0 + j)] = val;
+                        }
                     }
                 }
             }
@@ -578,7 +612,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
             int Fx[RC];
 #pragma unroll
             for (int jj = 0; jj < RC; jj += 4) {
-                const int4 f4 = *reinterpret_cast<const int4*>(&s_F[prev.stage][16 * q + RC * grp + jj]);
+                const int4 f4 = *reinterpret_cast<const int4*>(&s_F[prev.slot][16 * q + RC * grp + jj]);
                 Fx[jj] = f4.x;
                 Fx[jj + 1] = f4.y;
                 Fx[jj + 2] = f4.z;
@@ -616,26 +650,28 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
         }
     };
 
-    // Pre-sliced digit units of chunk cc of tile (entry, r0, c0) into stage stg:
-    // B's planes and column exponents, and (MODE 2) A's planes and row
-    // exponents, with 16-byte cp.async; one commit group.
-    auto copy_units = [&](int entry, int r0, int c0, int nch_e, int cc, int stg) {
+    // Pre-sliced digit units of chunk cc of tile (entry, r0, c0) into stage stg
+    // (planes) and exponent slot sl: B's planes and column exponents, and
+    // (MODE 2) A's planes and row exponents, with 16-byte cp.async; one commit
+    // group.
+    auto copy_units = [&](int entry, int r0, int c0, int nch_e, int cc, int stg, int sl) {
         uint8_t* pa = smem + stg * (S * (C_::planeA + C_::planeB));
         uint8_t* pb = pa + S * C_::planeA;
         if constexpr (MODE == 2) {
             const uint8_t* src = aunits + (size_t)(afirst[entry] + (long long)(r0 / kTM) * nch_e + cc) * C_::unitA;
             for (int o = 16 * tid; o < S * C_::planeA; o += 16 * kThreadsS) cp_async16(pa + o, src + o);
-            if (tid < kTM / 4) cp_async16(&s_E[stg][4 * tid], src + S * C_::planeA + 16 * tid);
+            if (tid < kTM / 4) cp_async16(&s_E[sl][4 * tid], src + S * C_::planeA + 16 * tid);
         }
         if constexpr (MODE >= 1) {
             const uint8_t* src = bunits + (size_t)(bfirst[entry] + (long long)(c0 / kTN) * nch_e + cc) * C_::unitB;
             for (int o = 16 * tid; o < S * C_::planeB; o += 16 * kThreadsS) cp_async16(pb + o, src + o);
-            if (tid < kTN / 4) cp_async16(&s_F[stg][4 * tid], src + S * C_::planeB + 16 * tid);
+            if (tid < kTN / 4) cp_async16(&s_F[sl][4 * tid], src + S * C_::planeB + 16 * tid);
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
 
     int iter = 0;
+    int slot = 0;             // iter mod 3: the chunk's exponent slot
     int last_commit = -1;     // iteration of the most recent tensor-core commit
     int t = blockIdx.x;
     if (tid < 8) {   // the first two records, synchronously
@@ -649,21 +685,21 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
         load_c0(r0.d, r0.row0, r0.col0);
         if constexpr (PRELOAD) load_chunk(r0.d, r0.row0, r0.col0, 0);
     }
-    int ti = 0;   // index of the CTA's current tile (its record is s_tile[ti % 3])
+    int ti = 0;   // index of the CTA's current tile (its record is s_tile[ti & 3])
     while (t < n_items) {
-        const STile& cur = s_tile[ti % 3];
+        const STile& cur = s_tile[ti & 3];
         const DevDesc d = cur.d;
         const int entry = cur.entry;
         const int m0 = cur.row0, n0 = cur.col0;
         const int nch = (d.k + KC - 1) / KC;
         const int tn = t + gridDim.x;
-        const STile& nxt = s_tile[(ti + 1) % 3];   // valid when tn < n_items
+        const STile& nxt = s_tile[(ti + 1) & 3];   // valid when tn < n_items
         {
-            // the record two tiles ahead into the ring slot the previous tile
-            // used (one commit group; waited for before this chunk's tensor-core
+            // the record two tiles ahead into the ring slot tile ti - 2 used
+            // (one commit group; waited for before this chunk's tensor-core
             // issue and visible to every thread after the barrier there)
             const int t2 = tn + gridDim.x;
-            if (tid < 4 && t2 < n_items) cp_async16(reinterpret_cast<uint4*>(&s_tile[(ti + 2) % 3]) + tid,
+            if (tid < 4 && t2 < n_items) cp_async16(reinterpret_cast<uint4*>(&s_tile[(ti + 2) & 3]) + tid,
                                                     reinterpret_cast<const uint4*>(tiles + t2) + tid);
             asm volatile("cp.async.commit_group;\n" ::: "memory");
             // the CTA's next tile into L2 while this one runs: its C (one
@@ -689,8 +725,9 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
                 }
             }
         }
-        for (int c = 0; c < nch; ++c, ++iter) {
+        for (int c = 0; c < nch; ++c, ++iter, slot = slot == 2 ? 0 : slot + 1) {
             const int stage = iter & 1;
+            const int slot_next = slot == 2 ? 0 : slot + 1;
             const int k0 = c * KC;
             uint8_t* planeA = smem + stage * (S * (C_::planeA + C_::planeB));
             uint8_t* planeB = planeA + S * C_::planeA;
@@ -699,7 +736,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
             // copies the next chunk's units one iteration ahead (step 6), so
             // only the CTA's first chunk copies its own here.
             if constexpr (PRE) {
-                if (MODE == 1 || iter == 0) copy_units(entry, m0, n0, nch, c, stage);
+                if (MODE == 1 || iter == 0) copy_units(entry, m0, n0, nch, c, stage, slot);
             }
             if constexpr (!PRELOAD && !preA) load_chunk(d, m0, n0, k0);
             // (1) a later chunk into L2 (with PRELOAD: the one after the next,
@@ -759,7 +796,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
                         const unsigned long long w = __shfl_xor_sync(0xffffffffu, mx, o);
                         mx = w > mx ? w : mx;
                     }
-                    if (lane == 0) s_F[stage][4 * warp + jc] = mx ? exp_of_bits(mx) : 0;
+                    if (lane == 0) s_F[slot][4 * warp + jc] = mx ? exp_of_bits(mx) : 0;
                 }
             }
             // row / column exponents exchanged; FAST: any quarter of tiny values
@@ -794,7 +831,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
                     for (int qq = 1; qq < 4; ++qq) mx = s_rmax[qq][rloc] > mx ? s_rmax[qq][rloc] : mx;
                     E = mx ? exp_of_bits(mx) : 0;
                 }
-                if (q == 0) s_E[stage][rloc] = E;
+                if (q == 0) s_E[slot][rloc] = E;
             }
             // (3) digits into the planes of this stage (free: their MMAs were
             // waited for when the previous chunk was recombined)
@@ -846,7 +883,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
 #pragma unroll
                 for (int jc = 0; jc < 4; ++jc) {
                     const int j = 4 * warp + jc;
-                    const int F = s_F[stage][j];
+                    const int F = s_F[slot][j];
                     uint8_t* dst = planeB + (j >> 3) * C_::sbo + (j & 7) * 16;
 #pragma unroll
                     for (int h = 0; h < KB; ++h) {
@@ -871,27 +908,31 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
             }
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             __syncthreads();
+            if (s_fail[(iter - 1) & 1]) {   // the previous chunk's recombination failed somewhere
+                failed = true;
+                break;
+            }
             // (4) one thread issues the chunk's tensor-core work
             if (tid == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                bool first_of_level[S + 2];
+                bool first_of_acc[NACC];
 #pragma unroll
-                for (int L = 0; L < S + 2; ++L) first_of_level[L] = true;
+                for (int g = 0; g < NACC; ++g) first_of_acc[g] = true;
 #pragma unroll
                 for (int s1 = 1; s1 <= S; ++s1) {
 #pragma unroll
                     for (int t1 = 1; t1 <= S; ++t1) {
                         if (s1 + t1 > S + 1) continue;
-                        const int L = s1 + t1;
-                        const uint32_t dcol = tmem + (uint32_t)(stage * S * kTN + (L - 2) * kTN);
+                        const int g = acc_of<FP16, S>(s1, t1);
+                        const uint32_t dcol = tmem + (uint32_t)(stage * NACC * kTN + g * kTN);
                         const uint32_t a_base = smem_u32(planeA + (s1 - 1) * C_::planeA);
                         const uint32_t b_base = smem_u32(planeB + (t1 - 1) * C_::planeB);
 #pragma unroll
                         for (int kq = 0; kq < KC / 16; ++kq) {
                             const uint64_t ad = make_desc(a_base + kq * 256, C_::sbo);
                             const uint64_t bd = make_desc(b_base + kq * 256, C_::sbo);
-                            const uint32_t accum = first_of_level[L] ? 0u : 1u;
-                            first_of_level[L] = false;
+                            const uint32_t accum = first_of_acc[g] ? 0u : 1u;
+                            first_of_acc[g] = false;
                             asm volatile(
                                 "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
@@ -907,12 +948,9 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
             // (5) recombine the previous chunk while this one runs
             if (have_prev) {
                 const bool ok = recombine((uint32_t)(((iter - 1) >> 1) & 1));
-                if (__syncthreads_or(!ok)) {
-                    failed = true;
-                    break;
-                }
+                if (!ok) s_fail[iter & 1] = 1;   // the CTA stops after the next barrier
                 if (prev.last) {
-                    store_prev();
+                    if (ok) store_prev();
                     load_c0(d, m0, n0);   // chunk c is chunk 0 of this tile; consumed next iteration
                 }
             }
@@ -920,9 +958,9 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
             // recombination just finished with (and the MMAs that read it are done)
             if constexpr (MODE == 2) {
                 if (c + 1 < nch) {
-                    copy_units(entry, m0, n0, nch, c + 1, stage ^ 1);
+                    copy_units(entry, m0, n0, nch, c + 1, stage ^ 1, slot_next);
                 } else if (tn < n_items) {
-                    copy_units(nxt.entry, nxt.row0, nxt.col0, (nxt.d.k + KC - 1) / KC, 0, stage ^ 1);
+                    copy_units(nxt.entry, nxt.row0, nxt.col0, (nxt.d.k + KC - 1) / KC, 0, stage ^ 1, slot_next);
                 }
             }
             prev.C = d.C;
@@ -933,6 +971,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
             prev.col0 = n0;
             prev.c = c;
             prev.stage = stage;
+            prev.slot = slot;
             prev.last = (c == nch - 1);
             have_prev = true;
         }
@@ -940,6 +979,8 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
         t = tn;
         ++ti;
     }
+    __syncthreads();
+    if (s_fail[0] | s_fail[1]) failed = true;   // set in the last iteration
     if (have_prev && !failed) {
         const bool ok = recombine((uint32_t)(((iter - 1) >> 1) & 1));
         if (__syncthreads_or(!ok)) failed = true;
