@@ -54,10 +54,11 @@ WORKLOAD = ("variable-size FP64 batch: 20,000 entries, b log-uniform [64,2048], 
 DFMA_LANES_PER_SM_CLK = 2          # FP64 FMA lanes per SM per clock on GB300 (1.25 TFLOP/s nominal)
 # DRAM bytes (read + write) per algorithmic byte of k_persistent on the
 # variable-size batch, from an ncu capture of a 1/20-scale case of the same
-# batch (same 4 GB pool), valid while fp64_tiles.cu has the SHA-256 prefix
-# below; None until captured.
-TRAFFIC_PER_ALG_BYTE = None
-TRAFFIC_SOURCE_SHA = None
+# batch (its first 1,000 entries, same 4 GB pool): 6.696 GB read + 2.316 GB
+# written for 7.356 GB algorithmic.  Valid while fp64_tiles.cu has the
+# SHA-256 prefix below (the roofline's traffic is null otherwise).
+TRAFFIC_PER_ALG_BYTE = 1.22503
+TRAFFIC_SOURCE_SHA = "c86a6ad4ee65ca25"
 
 
 def dist_env():
@@ -499,7 +500,7 @@ def main():
     if not args.no_extras and world == 1:
         ex = extras(L, handle, stream, dev, peak, timed, set(args.extras.split(",")), args, props)
         print("extras: " + json.dumps(ex), flush=True)
-        line["north_star"] = north_star_summary(ex)
+        line["targets"] = targets_summary(ex)
 
     if not args.no_cpu and rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline_variable(args.cpu_flops)
@@ -511,7 +512,7 @@ def main():
     return 0
 
 
-def north_star_summary(ex: dict) -> dict:
+def targets_summary(ex: dict) -> dict:
     """The named targets in a few fields: the split-precision error per preset
     and form (against the FP64 path) with its fraction of the HBM roof, and the
     serving latencies with their sample counts."""
