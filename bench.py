@@ -261,8 +261,8 @@ def cpu_baseline_variable(target_flops: float = 4e11) -> dict:
 
 def cpu_baseline_extras() -> dict:
     """The oracle, as it stands, on small samples of the other workloads
-    (same shapes and distributions), timed on the host cores: the uniform
-    sweep (the first 1/32 of every group), the paper's low-rank chain (2000
+    (same shapes and distributions), timed on the host cores: the small
+    O-form batch (whole), the uniform sweep (the first 1/32 of every group), the paper's low-rank chain (2000
     blocks, b 1024, r 16; the paper's flop count), the randomized SVD (4
     kernel-matrix blocks, 1024^2, r 16, l 26, q 1; the library's flop count)
     and the split-precision product (4 T-form entries, 1024 x 64 x 1024,
@@ -271,6 +271,10 @@ def cpu_baseline_extras() -> dict:
     from oracle import lowrank as OL
     from paper_2311_07602_gb300 import workloads as W
     out = {}
+    sm = W.small_o_form(device="cpu")
+    ff, ss, used = oracle_run(sm)
+    out["small_o_form"] = {"gflops": round(ff / ss / 1e9, 2), "ms": round(ss * 1e3, 2), "threads": used,
+                           "sample": "the whole batch (64 x 256x256x16)"}
     fl, secs, ents = 0.0, 0.0, 0
     for f, b, r, n, s in W.uniform_sweep_groups():
         cnt = max(1, n // 32)
@@ -499,6 +503,10 @@ def main():
     ex = {}
     if not args.no_extras and world == 1:
         ex = extras(L, handle, stream, dev, peak, timed, set(args.extras.split(",")), args, props)
+        if not args.no_cpu:
+            t0 = time.perf_counter()
+            ex["cpu_oracle"] = cpu_baseline_extras()
+            ex["cpu_oracle"]["seconds_total"] = round(time.perf_counter() - t0, 1)
         print("extras: " + json.dumps(ex), flush=True)
         line["targets"] = targets_summary(ex)
 

@@ -467,13 +467,14 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
     __shared__ __align__(16) int s_F[3][kTN];
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ __align__(8) uint64_t s_never;   // test_stall: a barrier nothing arrives on
-    // the records of the CTA's tiles in a ring of four: the record two tiles
-    // ahead is copied while a tile starts, so no tile waits on a global load
-    // of its own record.  Slot ti & 3 holds tile ti.  A thread that starts
-    // tile ti + 1 (and writes slot (ti + 3) & 3) may meet threads still in
-    // tile ti, which read slots ti & 3 and (ti + 1) & 3, never one still in
-    // tile ti - 1.
-    __shared__ __align__(16) STile s_tile[4];
+    // the records of the CTA's tiles in a ring of eight: the record three
+    // tiles ahead is copied while a tile starts, so no tile waits on a global
+    // load of its own record, and mode 2 (one chunk per tile in the usual
+    // case) need not wait for the copy it has just issued.  Slot ti & 7 holds
+    // tile ti.  A thread that starts tile ti + 1 (and writes slot (ti + 4) & 7)
+    // may meet threads still in tile ti, which read slots ti & 7 and
+    // (ti + 1) & 7, never one still in tile ti - 1.
+    __shared__ __align__(16) STile s_tile[8];
     __shared__ uint32_t s_tmem;
     // a recombination wait expired in an iteration of this parity: set before
     // the next iteration's issue barrier, read by every thread after it (a
@@ -674,7 +675,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
     int slot = 0;             // iter mod 3: the chunk's exponent slot
     int last_commit = -1;     // iteration of the most recent tensor-core commit
     int t = blockIdx.x;
-    if (tid < 8) {   // the first two records, synchronously
+    if (tid < 12) {   // the first three records, synchronously
         const int tt = t + (tid >> 2) * (int)gridDim.x;
         if (tt < n_items)
             reinterpret_cast<uint4*>(&s_tile[tid >> 2])[tid & 3] = reinterpret_cast<const uint4*>(tiles + tt)[tid & 3];
@@ -685,22 +686,24 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
         load_c0(r0.d, r0.row0, r0.col0);
         if constexpr (PRELOAD) load_chunk(r0.d, r0.row0, r0.col0, 0);
     }
-    int ti = 0;   // index of the CTA's current tile (its record is s_tile[ti & 3])
+    int ti = 0;   // index of the CTA's current tile (its record is s_tile[ti & 7])
     while (t < n_items) {
-        const STile& cur = s_tile[ti & 3];
+        const STile& cur = s_tile[ti & 7];
         const DevDesc d = cur.d;
         const int entry = cur.entry;
         const int m0 = cur.row0, n0 = cur.col0;
         const int nch = (d.k + KC - 1) / KC;
         const int tn = t + gridDim.x;
-        const STile& nxt = s_tile[(ti + 1) & 3];   // valid when tn < n_items
+        const STile& nxt = s_tile[(ti + 1) & 7];   // valid when tn < n_items
         {
-            // the record two tiles ahead into the ring slot tile ti - 2 used
-            // (one commit group; waited for before this chunk's tensor-core
-            // issue and visible to every thread after the barrier there)
-            const int t2 = tn + gridDim.x;
-            if (tid < 4 && t2 < n_items) cp_async16(reinterpret_cast<uint4*>(&s_tile[(ti + 2) & 3]) + tid,
-                                                    reinterpret_cast<const uint4*>(tiles + t2) + tid);
+            // the record three tiles ahead into the ring slot tile ti - 5 used
+            // (one commit group; complete before the tensor-core issue of this
+            // tile's second chunk or of the next tile's first, and visible to
+            // every thread after the barrier there, so before tile ti + 2 reads
+            // it as its next tile)
+            const int t3 = tn + 2 * (int)gridDim.x;
+            if (tid < 4 && t3 < n_items) cp_async16(reinterpret_cast<uint4*>(&s_tile[(ti + 3) & 7]) + tid,
+                                                    reinterpret_cast<const uint4*>(tiles + t3) + tid);
             asm volatile("cp.async.commit_group;\n" ::: "memory");
             // the CTA's next tile into L2 while this one runs: its C (one
             // 128-byte line of 16 rows per thread) and, when pre-sliced, its
@@ -733,7 +736,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
             uint8_t* planeB = planeA + S * C_::planeA;
             // (0) pre-sliced units.  MODE 1 copies this chunk's B here, where the
             // copy overlaps the slicing of A; MODE 2 (nothing else to overlap)
-            // copies the next chunk's units one iteration ahead (step 6), so
+            // copies the next chunk's units one iteration ahead (step 5), so
             // only the CTA's first chunk copies its own here.
             if constexpr (PRE) {
                 if (MODE == 1 || iter == 0) copy_units(entry, m0, n0, nch, c, stage, slot);
@@ -878,7 +881,14 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
                     }
                 }
             }
-            asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // units and the tile record
+            // this chunk's units (and older copies).  Mode 2's first chunk of a
+            // tile (after the CTA's first): its units were committed one
+            // iteration ago and the newest group is the record just issued at
+            // the tile's start, which may stay in flight for another iteration.
+            if (MODE == 2 && c == 0 && iter > 0)
+                asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+            else
+                asm volatile("cp.async.wait_group 0;\n" ::: "memory");
             if constexpr (!PRE) {
 #pragma unroll
                 for (int jc = 0; jc < 4; ++jc) {
@@ -945,22 +955,30 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
                              : "memory");
             }
             last_commit = iter;
-            // (5) recombine the previous chunk while this one runs
+            const uint32_t parity_prev = (uint32_t)(((iter - 1) >> 1) & 1);
+            bool prev_done = true;
+            // (5) MODE 2: the next chunk's units into the other stage as soon as
+            // the previous chunk's tensor-core work (which read its planes) is
+            // done, so the copy runs during the recombination (the recombination's
+            // own wait on the same phase then returns at once)
+            if constexpr (MODE == 2) {
+                if (have_prev)
+                    prev_done = __all_sync(0xffffffffu, mbar_wait(smem_u32(&s_bar[prev.stage]), parity_prev));
+                if (prev_done) {
+                    if (c + 1 < nch) {
+                        copy_units(entry, m0, n0, nch, c + 1, stage ^ 1, slot_next);
+                    } else if (tn < n_items) {
+                        copy_units(nxt.entry, nxt.row0, nxt.col0, (nxt.d.k + KC - 1) / KC, 0, stage ^ 1, slot_next);
+                    }
+                }
+            }
+            // (6) recombine the previous chunk while this one runs
             if (have_prev) {
-                const bool ok = recombine((uint32_t)(((iter - 1) >> 1) & 1));
+                const bool ok = prev_done && recombine(parity_prev);
                 if (!ok) s_fail[iter & 1] = 1;   // the CTA stops after the next barrier
                 if (prev.last) {
                     if (ok) store_prev();
                     load_c0(d, m0, n0);   // chunk c is chunk 0 of this tile; consumed next iteration
-                }
-            }
-            // (6) MODE 2: the next chunk's units into the other stage, which the
-            // recombination just finished with (and the MMAs that read it are done)
-            if constexpr (MODE == 2) {
-                if (c + 1 < nch) {
-                    copy_units(entry, m0, n0, nch, c + 1, stage ^ 1, slot_next);
-                } else if (tn < n_items) {
-                    copy_units(nxt.entry, nxt.row0, nxt.col0, (nxt.d.k + KC - 1) / KC, 0, stage ^ 1, slot_next);
                 }
             }
             prev.C = d.C;
