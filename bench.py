@@ -948,7 +948,8 @@ def e2e_leg(L, batches, steps, warmup, barrier, max_over_ranks, world, dev_index
     each batch's entries (host memory is shared by the ranks); flops count
     what ran.  Also reported: the per-engine breakdown of the last call
     (lrb_execute_host_get_timing), the pinned-copy rates of a single large
-    copy each way, and where the pinned pages live relative to the GPU."""
+    copy each way from a fresh pinned buffer and from the caller's own
+    buffers, and where the pinned pages live relative to the GPU."""
     import torch
     handle = L.Handle(dev_index)
     rows, hold = [], []
@@ -1029,6 +1030,27 @@ def e2e_leg(L, batches, steps, warmup, barrier, max_over_ranks, world, dev_index
     secs = max_over_ranks(time.perf_counter() - t0)
     tm = handle.host_timing()
     handle.close()
+    # the same single large copies from and into the caller's own pinned
+    # buffers (the operand pool in, the start of C out), after the timed
+    # region: a fresh pinned buffer can copy at full rate while these do not
+    torch.cuda.synchronize()
+    own_gbs = {}
+    for name, hb, to_dev in (("pool_h2d", hA, True), ("C_d2h", hC, False)):
+        n_el = min(hb.numel(), (4 << 30) // 8)
+        dbuf = torch.empty(n_el, dtype=torch.float64, device="cuda")
+        best = 0.0
+        for rep in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            if to_dev:
+                dbuf.copy_(hb[:n_el], non_blocking=True)
+            else:
+                hb[:n_el].copy_(dbuf, non_blocking=True)
+            e1.record()
+            torch.cuda.synchronize()
+            best = max(best, 8 * n_el / (e0.elapsed_time(e1) / 1e3) / 1e9)
+        own_gbs[name] = round(best, 1)
+        del dbuf
     h2d = int(tm["h2d_bytes"])
     d2h = int(tm["d2h_bytes"])
     all_fl = sum_over_ranks(fl) if strong else world * fl
@@ -1050,7 +1072,7 @@ def e2e_leg(L, batches, steps, warmup, barrier, max_over_ranks, world, dev_index
                           "copies_after_last_launch_ms": round(tm["compute_end_to_last_ms"], 1),
                           "first_piece_h2d_ms": round(tm["first_h2d_ms"], 1),
                           "first_piece_h2d_gb": round(tm["first_h2d_bytes"] / 1e9, 3)},
-            "pinned_copy_gbs": copy_gbs, "host": topo, "pinned_page_nodes": pages,
+            "pinned_copy_gbs": copy_gbs, "caller_buffer_copy_gbs": own_gbs, "host": topo, "pinned_page_nodes": pages,
             "api": "lrb_execute_host (pinned host buffers; copies in, compute and copies out pipelined in pieces)"}
 
 
