@@ -361,7 +361,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads")
-    ap.add_argument("--extras", default="sweep,small,split,serving,dmma,lr,blr,lowrank",
+    ap.add_argument("--extras", default="sweep,small,split,split_var,serving,dmma,lr,blr,lowrank",
                     help="comma-separated subset of the other workloads (also: sweep_e2e)")
     ap.add_argument("--split-batch", type=int, default=2048, help="entries of the split-precision batch")
     ap.add_argument("--dmma-scale", type=float, default=0.25, help="batch-count scale of the DMMA comparison")
@@ -565,6 +565,8 @@ def extras(L, handle, stream, dev, peak_fp64, timed, which, args, props):
         out["small_o_form"] = small_leg(L, handle, stream, dev, peak_fp64)
     if "split" in which:
         out["split"] = split_leg(L, handle, dev, timed, hbm, args.split_batch)
+    if "split_var" in which:
+        out["split_variable"] = split_var_leg(L, handle, dev, timed, args.count)
     if "serving" in which:
         out["serving"] = serving_leg(L, handle, dev, peak_fp64, args.serving_secs, args.overload_secs)
     if "dmma" in which:
@@ -581,9 +583,11 @@ def extras(L, handle, stream, dev, peak_fp64, timed, which, args, props):
 
 def sweep_leg(L, handle, dev, peak_fp64, timed, scale=1.0):
     """The uniform-shape sweep (b in {256, 512, 1024} x r in {16, 32, 64} x
-    both forms, 32,256 entries, N(0,1)) as one persistent graph launch, and
-    through one launch per shape."""
+    both forms, 32,256 entries, N(0,1)) as one persistent graph launch,
+    through one launch per shape, and every (form, b, r) group as a plan of
+    its own."""
     import torch
+    from paper_2311_07602_gb300 import workloads as W
     batches = sweep_batches(dev, scale)
     descs = np.concatenate([L.descs_for(b) for b in batches])
     f = float(sum(b.flops() for b in batches))
@@ -591,13 +595,23 @@ def sweep_leg(L, handle, dev, peak_fp64, timed, scale=1.0):
         info = p.info()
         ms, _ = timed(lambda s: p.launch(s), 5, 3)
         ms_q, _ = timed(lambda s: p.launch_plain(s), 3, 3)
+    # every (form, b, r) group on its own: one persistent graph launch each
+    groups = []
+    for (form, b, r, n, _), bt in zip(W.uniform_sweep_groups(), batches):
+        fg = bt.flops()
+        with handle.plan(L.descs_for(bt), use_graph=True) as pg:
+            ms_g, _ = timed(lambda s: pg.launch(s), 3, 3)
+        groups.append({"form": "T" if form == W.FORM_T else "O", "b": b, "r": r, "batch": len(bt),
+                       "ms": round(ms_g / 3, 3), "gflops": round(fg * 3 / ms_g / 1e6, 1),
+                       "frac_fp64_peak": round(fg * 3 / ms_g / 1e9 / peak_fp64, 4)})
     del batches
     torch.cuda.empty_cache()
     return {"workload": "b in {256,512,1024} (batch 4096/1024/256) x r in {16,32,64} x T/O, N(0,1)"
                         + ("" if scale == 1.0 else f" (batch counts x {scale})"),
             "gflops": round(f * 5 / ms / 1e6, 1), "ms": round(ms / 5, 3),
             "frac_fp64_peak": round(f * 5 / ms / 1e9 / peak_fp64, 4),
-            "plain_gflops": round(f * 3 / ms_q / 1e6, 1), "plain_launches": int(info["groups"])}
+            "plain_gflops": round(f * 3 / ms_q / 1e6, 1), "plain_launches": int(info["groups"]),
+            "groups": groups}
 
 
 def lowrank_leg(L, handle, dev, peak_fp64, timed, count=1024, b=1024, r=16, p=10, q=1):
@@ -801,6 +815,43 @@ def small_leg(L, handle, stream, dev, peak_fp64):
     ms = statistics.median(per)
     return {"workload": "O-form, 64 x C(256x256) += A(256x16) B(16x256), U[-1,1], seed 0, L2 flushed",
             "gflops": round(f / ms / 1e6, 2), "ms": round(ms, 4), "frac_fp64_peak": round(f / ms / 1e9 / peak_fp64, 4)}
+
+
+def split_var_leg(L, handle, dev, timed, count=VARIABLE_COUNT):
+    """The variable-size batch of the headline in split precision (BF16,
+    S = 3): one plan over all entries (pre-passes and both kernel modes in
+    one launch), its FP64-equivalent rate, and its error against the FP64
+    path from the same C: relative Frobenius norm of the difference of the
+    two results over the norm of the FP64 product A B, over the whole batch."""
+    import torch
+    vb = variable_workload(dev, count)
+    f = vb.flops()
+    descs = L.descs_for(vb)
+    c0 = vb.C.clone()
+    out = {"workload": "the headline's variable-size batch (%d entries, N(0,1)), BF16 S = 3" % len(vb)}
+    with handle.plan(descs, precision=L.LRB_PREC_SPLIT_BF16_S3) as p:
+        info = p.info()
+        p.launch()
+        torch.cuda.synchronize()
+        st = p.status()
+        cs = vb.C.clone()
+        ms, _ = timed(lambda s: p.launch(s), 3, 3)
+    vb.C.copy_(c0)
+    with handle.plan(descs, use_graph=True) as p:
+        p.launch()
+        torch.cuda.synchronize()
+    num = den = 0.0
+    step = 1 << 27
+    for i in range(0, vb.C.numel(), step):
+        cf = vb.C[i:i + step]
+        num += float(torch.sum((cs[i:i + step] - cf) ** 2))
+        den += float(torch.sum((cf - c0[i:i + step]) ** 2))
+    out.update({"ms": round(ms / 3, 3), "tflops_fp64_equiv": round(f * 3 / ms / 1e9, 2),
+                "items": int(info["items"]), "rel_fro_err_vs_fp64_product": float(f"{(num / den) ** 0.5:.3g}"),
+                "status": int(st)})
+    del vb, c0, cs
+    torch.cuda.empty_cache()
+    return out
 
 
 def split_leg(L, handle, dev, timed, hbm, batch):
