@@ -8,6 +8,7 @@
 // persistent kernel pulls tiles from a device-side counter, largest first.
 #include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -401,15 +402,44 @@ void save_cache(lrb_handle* h) {
 }
 
 // Time each candidate variant on a uniform batch of the bucket's central
-// shape (plain launches, 2 repetitions after a warm-up) and keep the fastest.
+// shape in the kernel a tuned plan runs -- the slim persistent kernel, 5 CTAs
+// per SM, pulling tiles from a counter -- one warm-up launch and the best of
+// two timed ones, and keep the fastest.  The batch has about 3 GFLOP and at
+// least four waves of the persistent grid for every candidate (so tall tiles
+// are not charged for a partly empty last wave that a large batch would not
+// have); its operands are zeros in the handle's scratch buffer (at most 1 GB).
 lrb_status tune_bucket(lrb_handle* h, int m, int n, int k, bool dmma_ok, int* best) {
     const int M = bucket_center(bucket(m)), N = bucket_center(bucket(n)), K = bucket_center(bucket(k));
     const double flops_entry = 2.0 * M * N * K;
     const double bytes_entry = 8.0 * ((double)M * K + (double)K * N + (double)M * N);
-    int E = (int)std::ceil(3e9 / flops_entry);
-    E = std::max(1, std::min(E, (int)(512e6 / bytes_entry)));
-    E = std::max(E, 1);
-    const size_t need = (size_t)(bytes_entry * E) + 4096 + (size_t)E * (sizeof(DevDesc) + 4);
+    *best = heuristic_variant(m, n, k, dmma_ok);
+    std::vector<int> cand;
+    for (int v = 0; v < kNumVariants; ++v) {
+        const Variant& V = kVariants[v];
+        if (variant_set(v) != 0) continue;   // tuned plans run in the slim persistent kernel (5 CTAs/SM)
+        if (V.dmma && !dmma_ok) continue;
+        // skip tiles more than twice as tall/wide as the shape needs
+        if (V.bm() > 32 && V.bm() >= 2 * std::max(M, 32)) continue;
+        if (V.bn() > 8 && V.bn() >= 2 * std::max(N, 8)) continue;
+        cand.push_back(v);
+    }
+    if (cand.empty()) return LRB_OK;
+    const int grid_full = std::max(1, h->sms * h->blocks_per_sm_slim);
+    long long min_tiles = LLONG_MAX, max_tiles = 0;
+    for (int v : cand) {
+        const long long t = (long long)ceil_div(M, kVariants[v].bm()) * ceil_div(N, kVariants[v].bn());
+        min_tiles = std::min(min_tiles, t);
+        max_tiles = std::max(max_tiles, t);
+    }
+    long long E = (long long)std::ceil(3e9 / flops_entry);
+    E = std::max(E, (4LL * grid_full + min_tiles - 1) / min_tiles);
+    E = std::min(E, std::max(1LL, (long long)(1e9 / bytes_entry)));
+    E = std::max(E, 1LL);
+    const size_t op_bytes = (size_t)(bytes_entry * (double)E);
+    const size_t desc_off = (op_bytes + 255) & ~(size_t)255;
+    const size_t item_off = (desc_off + sizeof(DevDesc) * (size_t)E + 255) & ~(size_t)255;
+    const size_t head_off = (item_off + sizeof(Item) * (size_t)(E * max_tiles) + 255) & ~(size_t)255;
+    const size_t need = head_off + 256;
     if (need > h->scratch_bytes) {
         if (h->scratch) cudaFree(h->scratch);
         h->scratch = nullptr;
@@ -418,52 +448,60 @@ lrb_status tune_bucket(lrb_handle* h, int m, int n, int k, bool dmma_ok, int* be
         h->scratch_bytes = need;
     }
     char* base = (char*)h->scratch;
-    LRB_CUDA(cudaMemsetAsync(base, 0, need, h->stream));
-    std::vector<DevDesc> dd(E);
-    std::vector<int32_t> ent(E);
+    LRB_CUDA(cudaMemsetAsync(base, 0, op_bytes, h->stream));
+    std::vector<DevDesc> dd((size_t)E);
     double* A = (double*)base;
     double* B = A + (size_t)M * K * E;
     double* C = B + (size_t)K * N * E;
-    for (int e = 0; e < E; ++e) {
+    for (long long e = 0; e < E; ++e)
         dd[e] = DevDesc{A + (size_t)M * K * e, B + (size_t)K * N * e, C + (size_t)M * N * e, M, N, K, M, K, M};
-        ent[e] = e;
-    }
-    char* tail = (char*)(C + (size_t)M * N * E);
-    tail = (char*)(((uintptr_t)tail + 255) & ~(uintptr_t)255);
-    DevDesc* d_dd = (DevDesc*)tail;
-    int32_t* d_ent = (int32_t*)(tail + sizeof(DevDesc) * E);
-    LRB_CUDA(cudaMemcpyAsync(d_dd, dd.data(), sizeof(DevDesc) * E, cudaMemcpyHostToDevice, h->stream));
-    LRB_CUDA(cudaMemcpyAsync(d_ent, ent.data(), sizeof(int32_t) * E, cudaMemcpyHostToDevice, h->stream));
+    DevDesc* d_dd = (DevDesc*)(base + desc_off);
+    Item* d_items = (Item*)(base + item_off);
+    int* d_head = (int*)(base + head_off);
+    LRB_CUDA(cudaMemcpyAsync(d_dd, dd.data(), sizeof(DevDesc) * (size_t)E, cudaMemcpyHostToDevice, h->stream));
     cudaEvent_t e0, e1;
     LRB_CUDA(cudaEventCreate(&e0));
     LRB_CUDA(cudaEventCreate(&e1));
+    auto fail_with = [&](cudaError_t ce, const char* what) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return cuda_fail(ce, what);
+    };
     float best_ms = 1e30f;
-    *best = heuristic_variant(m, n, k, dmma_ok);
-    for (int v = 0; v < kNumVariants; ++v) {
+    std::vector<Item> items;
+    for (int v : cand) {
         const Variant& V = kVariants[v];
-        if (variant_set(v) != 0) continue;   // tuned plans run in the slim persistent kernel (5 CTAs/SM)
-        if (V.dmma && !dmma_ok) continue;
-        // skip tiles more than twice as tall/wide as the shape needs
-        if (V.bm() > 32 && V.bm() >= 2 * std::max(M, 32)) continue;
-        if (V.bn() > 8 && V.bn() >= 2 * std::max(N, 8)) continue;
-        const int tm = ceil_div(M, V.bm()), tn = ceil_div(N, V.bn());
-        cudaError_t ce = launch_plain_group(v, d_dd, d_ent, E, tm, tn, h->stream);
-        if (ce != cudaSuccess) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            return cuda_fail(ce, "tuning launch");
-        }
+        const int bm = V.bm(), bn = V.bn();
+        // the tiles in the planner's order: longest first (full tiles before edge tiles)
+        items.clear();
+        std::vector<double> cost;
+        for (long long e = 0; e < E; ++e)
+            for (int c0 = 0; c0 < N; c0 += bn)
+                for (int r0 = 0; r0 < M; r0 += bm) {
+                    items.push_back(Item{(int32_t)e, r0, c0, v});
+                    cost.push_back(tile_cost(V, std::min(bm, M - r0), std::min(bn, N - c0), K));
+                }
+        std::vector<size_t> order(items.size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+        std::vector<Item> sorted(items.size());
+        for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[order[i]];
+        items.swap(sorted);
+        const int n_items = (int)items.size();
+        cudaError_t ce = cudaMemcpyAsync(d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice,
+                                         h->stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);   // items is reused for the next candidate
+        if (ce != cudaSuccess) return fail_with(ce, "tuning upload");
+        const int grid = std::max(1, std::min(grid_full, n_items));
+        ce = launch_persistent(d_dd, d_items, n_items, d_head, grid, h->stream, 0, 0);
+        if (ce != cudaSuccess) return fail_with(ce, "tuning launch");
         float ms_min = 1e30f;
         for (int rep = 0; rep < 2; ++rep) {
             cudaEventRecord(e0, h->stream);
-            launch_plain_group(v, d_dd, d_ent, E, tm, tn, h->stream);
+            launch_persistent(d_dd, d_items, n_items, d_head, grid, h->stream, 0, 0);
             cudaEventRecord(e1, h->stream);
             ce = cudaEventSynchronize(e1);
-            if (ce != cudaSuccess) {
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                return cuda_fail(ce, "tuning run");
-            }
+            if (ce != cudaSuccess) return fail_with(ce, "tuning run");
             float ms = 0;
             cudaEventElapsedTime(&ms, e0, e1);
             ms_min = std::min(ms_min, ms);
@@ -634,7 +672,7 @@ lrb_status lrb_create(lrb_handle** out, int device) {
     int drv = 0;
     cudaDriverGetVersion(&drv);
     char key[256];
-    std::snprintf(key, sizeof key, "%s|cc%d%d|drv%d|lib1", prop.name, prop.major, prop.minor, drv);
+    std::snprintf(key, sizeof key, "%s|cc%d%d|drv%d|lib2", prop.name, prop.major, prop.minor, drv);
     h->gpu_key = key;
     if (const char* p = std::getenv("LRB_TUNE_CACHE")) h->cache_path = p;
     load_cache(h);
