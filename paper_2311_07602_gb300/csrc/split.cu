@@ -446,6 +446,16 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem_dst)), "l"(src) : "memory");
 }
 
+// One bulk (TMA) copy of `bytes` (a multiple of 16, both addresses 16-byte
+// aligned) from global to this CTA's shared memory, completing on mbarrier
+// `bar` (the caller has announced the bytes with expect_tx).
+__device__ __forceinline__ void bulk_copy(void* smem_dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(smem_dst)),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
 // One CTA per SM, 512 threads, tiles taken round-robin (tile = 128 x 64
 // outputs).  The k-chunks of all of a CTA's tiles form one pipeline: while
 // the tensor cores run chunk i (digit planes and TMEM accumulator set i&1),
@@ -490,6 +500,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
     __shared__ __align__(16) int s_E[3][kTM];
     __shared__ __align__(16) int s_F[3][kTN];
     __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ __align__(8) uint64_t s_ubar[2];   // pre-sliced units copied into each stage (bulk copies)
     __shared__ __align__(8) uint64_t s_never;   // test_stall: a barrier nothing arrives on
     // the records of the CTA's tiles in a ring of eight: the record three
     // tiles ahead is copied while a tile starts, so no tile waits on a global
@@ -519,6 +530,8 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s_bar[0])));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s_bar[1])));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s_never)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s_ubar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s_ubar[1])));
         s_fail[0] = s_fail[1] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
@@ -693,22 +706,51 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
 
     // Pre-sliced digit units of chunk cc of tile (entry, r0, c0) into stage stg
     // (planes) and exponent slot sl: B's planes and column exponents, and
-    // (MODE 2) A's planes and row exponents, with 16-byte cp.async; one commit
-    // group.
+    // (MODE 2) A's planes and row exponents.
+    // Copied by every thread in 16-byte pieces with cp.async (one commit
+    // group), or, with BULK (mode 2 with at most 80 KB of units per stage:
+    // BF16 S = 3 and the FP16 presets), by one thread as bulk (TMA) copies that
+    // complete on the stage's unit barrier s_ubar[stg].  Measured: bulk copies
+    // 2-3 % faster in mode 2 with those units, 3 % slower with BF16 S = 4's
+    // 99 KB, and 1.4 % slower in mode 1, where the per-thread copies overlap
+    // the slicing of A.  With BULK every thread counts the copies per stage
+    // (ucount), which gives the phase to wait for.  A stage is refilled only
+    // after the tensor-core work that read it has completed, and every thread
+    // has waited for the previous fill before that work was issued, so a
+    // phase is never reused early.
+    constexpr bool BULK = MODE == 2 && C_::unitA + C_::unitB <= 80 * 1024;
+    uint32_t ucount[2] = {0u, 0u};
     auto copy_units = [&](int entry, int r0, int c0, int nch_e, int cc, int stg, int sl) {
-        uint8_t* pa = smem + stg * (S * (C_::planeA + C_::planeB));
-        uint8_t* pb = pa + S * C_::planeA;
-        if constexpr (MODE == 2) {
-            const uint8_t* src = aunits + (size_t)(afirst[entry] + (long long)(r0 / kTM) * nch_e + cc) * C_::unitA;
-            for (int o = 16 * tid; o < S * C_::planeA; o += 16 * kThreadsS) cp_async16(pa + o, src + o);
-            if (tid < kTM / 4) cp_async16(&s_E[sl][4 * tid], src + S * C_::planeA + 16 * tid);
-        }
-        if constexpr (MODE >= 1) {
+        if constexpr (!BULK) {
+            uint8_t* pa = smem + stg * (S * (C_::planeA + C_::planeB));
+            uint8_t* pb = pa + S * C_::planeA;
+            if constexpr (MODE == 2) {
+                const uint8_t* src = aunits + (size_t)(afirst[entry] + (long long)(r0 / kTM) * nch_e + cc) * C_::unitA;
+                for (int o = 16 * tid; o < S * C_::planeA; o += 16 * kThreadsS) cp_async16(pa + o, src + o);
+                if (tid < kTM / 4) cp_async16(&s_E[sl][4 * tid], src + S * C_::planeA + 16 * tid);
+            }
             const uint8_t* src = bunits + (size_t)(bfirst[entry] + (long long)(c0 / kTN) * nch_e + cc) * C_::unitB;
             for (int o = 16 * tid; o < S * C_::planeB; o += 16 * kThreadsS) cp_async16(pb + o, src + o);
             if (tid < kTN / 4) cp_async16(&s_F[sl][4 * tid], src + S * C_::planeB + 16 * tid);
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+        } else {
+            if (tid == 0) {
+                uint8_t* pa = smem + stg * (S * (C_::planeA + C_::planeB));
+                uint8_t* pb = pa + S * C_::planeA;
+                const uint32_t bar = smem_u32(&s_ubar[stg]);
+                constexpr uint32_t bytes = (MODE == 2 ? (uint32_t)C_::unitA : 0u) + (uint32_t)C_::unitB;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+                if constexpr (MODE == 2) {
+                    const uint8_t* src = aunits + (size_t)(afirst[entry] + (long long)(r0 / kTM) * nch_e + cc) * C_::unitA;
+                    bulk_copy(pa, src, S * C_::planeA, bar);
+                    bulk_copy(&s_E[sl][0], src + S * C_::planeA, 4 * kTM, bar);
+                }
+                const uint8_t* src = bunits + (size_t)(bfirst[entry] + (long long)(c0 / kTN) * nch_e + cc) * C_::unitB;
+                bulk_copy(pb, src, S * C_::planeB, bar);
+                bulk_copy(&s_F[sl][0], src + S * C_::planeB, 4 * kTN, bar);
+            }
+            ++ucount[stg];
         }
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
 
     int iter = 0;
@@ -920,14 +962,21 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
                     }
                 }
             }
-            // this chunk's units (and older copies).  Mode 2's first chunk of a
-            // tile (after the CTA's first): its units were committed one
-            // iteration ago and the newest group is the record just issued at
-            // the tile's start, which may stay in flight for another iteration.
-            if (MODE == 2 && c == 0 && iter > 0)
+            // This chunk's units and the tile records.  Mode 2's first chunk of
+            // a tile (after the CTA's first) need not wait for the newest cp.async
+            // group, the record just issued at the tile's start (needed two
+            // tiles later): its units came one iteration earlier, by cp.async
+            // or, with BULK, by bulk copies on the stage's unit barrier.  A unit
+            // wait that expires stops the CTA after the barrier below, before
+            // any tensor-core work reads the stage.
+            if (MODE == 2 && (BULK || (c == 0 && iter > 0)))
                 asm volatile("cp.async.wait_group 1;\n" ::: "memory");
             else
                 asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+            if constexpr (BULK) {
+                if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&s_ubar[stage]), (ucount[stage] - 1u) & 1u)))
+                    s_fail[(iter - 1) & 1] = 1;
+            }
             if constexpr (!PRE) {
 #pragma unroll
                 for (int jc = 0; jc < 4; ++jc) {
@@ -1051,6 +1100,10 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
         if (tid == 0) atomicExch(status, 1);
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // no copy may land after the CTA exits
+    if constexpr (BULK) {   // nor a bulk copy: the last fill of each stage (bounded)
+        for (int sg = 0; sg < 2; ++sg)
+            if (ucount[sg] > 0u) mbar_wait(smem_u32(&s_ubar[sg]), (ucount[sg] - 1u) & 1u);
+    }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
