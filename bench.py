@@ -54,11 +54,12 @@ WORKLOAD = ("variable-size FP64 batch: 20,000 entries, b log-uniform [64,2048], 
 DFMA_LANES_PER_SM_CLK = 2          # FP64 FMA lanes per SM per clock on GB300 (1.25 TFLOP/s nominal)
 # DRAM bytes (read + write) per algorithmic byte of k_persistent on the
 # variable-size batch, from an ncu capture of a 1/20-scale case of the same
-# batch (its first 1,000 entries, same 4 GB pool): 6.696 GB read + 2.316 GB
-# written for 7.356 GB algorithmic.  Valid while fp64_tiles.cu has the
-# SHA-256 prefix below (the roofline's traffic is null otherwise).
-TRAFFIC_PER_ALG_BYTE = 1.22503
-TRAFFIC_SOURCE_SHA = "c86a6ad4ee65ca25"
+# batch (its first 1,000 entries, same 4 GB pool): 6.716 GB read + 2.323 GB
+# written for 7.356 GB algorithmic.  Valid while the kernels (fp64_tiles.cu)
+# and the planner and tuner that choose their tiles (api.cu) have the SHA-256
+# prefix below (the roofline's traffic is null otherwise).
+TRAFFIC_PER_ALG_BYTE = 1.22873
+TRAFFIC_SOURCE_SHA = "6a71bc57959e9337"
 
 
 def dist_env():
@@ -120,9 +121,12 @@ def derived_fp64_peak_tflops(sms, mhz) -> float:
 
 
 def kernel_sha() -> str:
+    """SHA-256 prefix of the FP64 tile kernels and of the planner that picks their tiles."""
     import hashlib
-    path = os.path.join(ROOT, "paper_2311_07602_gb300", "csrc", "fp64_tiles.cu")
-    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in ("fp64_tiles.cu", "api.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2311_07602_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def fp64_probe(L, dev_index: int, seconds: float = 2.0) -> dict:

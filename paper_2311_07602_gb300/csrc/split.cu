@@ -32,9 +32,11 @@
 // groups); one thread issues tcgen05.mma (M 128, N 64, K 16) for every kept
 // pair into one of two TMEM accumulator sets and commits to that stage's
 // mbarrier; then the threads recombine the previous chunk from the other
-// set.  Every wait is bounded (2 s): on expiry the kernel records an error in
-// the plan's status word, drains its tensor-core work (bounded), releases
-// its TMEM and returns.
+// set.  Pre-sliced digit units (a plan's pre-passes) are copied into the
+// stages with cp.async or, in mode 2, with bulk (TMA) copies on per-stage
+// mbarriers.  Every wait is bounded (2 s): on expiry the kernel records an
+// error in the plan's status word, drains its tensor-core work and copies
+// (bounded), releases its TMEM and returns.
 #include <cuda_fp16.h>
 
 #include <algorithm>

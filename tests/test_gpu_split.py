@@ -193,12 +193,16 @@ def test_full_size_sampled(handle, name, form):
     torch.cuda.empty_cache()
 
 
-def test_bounded_wait_expiry_reports_timeout(handle):
+@pytest.mark.parametrize("shapes", [[(128, 64, 130), (100, 64, 200)], [(200, 130, 64), (100, 90, 70)]],
+                         ids=["one-column-tile", "pre-sliced-A"])
+def test_bounded_wait_expiry_reports_timeout(handle, shapes):
     """Failure path without a GPU fault: with test_stall the kernel also waits
     on a barrier nothing arrives on; its 2 s bound expires, it drains its own
-    tensor-core work, frees TMEM, leaves its C tiles unwritten and sets the
-    plan's status word; the context stays usable for the next plan."""
-    b = wide(ragged_batch([(128, 64, 130), (100, 64, 200)], pad=0, seed=71))
+    tensor-core work and its copies in flight, frees TMEM, leaves its C tiles
+    unwritten and sets the plan's status word; the context stays usable for
+    the next plan.  The second batch's entries have several column tiles, so
+    A comes pre-sliced and its units arrive by bulk copies."""
+    b = wide(ragged_batch(shapes, pad=0, seed=71))
     Ah, Bh, C0 = host(b.A), host(b.B), host(b.C)
     dev = b.to("cuda")
     with handle.plan(L.descs_for(dev), precision=PREC["bf16_s3"], test_stall=True) as plan:
