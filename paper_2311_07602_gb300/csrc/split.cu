@@ -324,56 +324,65 @@ __device__ __forceinline__ long long level_integer(const uint32_t (&v)[n_acc<FP1
     }
 }
 
-// The B part of one chunk, by 512 threads (warp w: columns 4w .. 4w + 3; lane:
-// k values lane + 32 h): column exponents F (to F_out[64]) and the S digit
-// planes (to planes, in the core-matrix layout the MMA reads).  Used by the
-// pre-pass, which writes to global memory; both use the same digit functions
-// as the in-kernel slicing, so the digits are the same whichever runs.
+// The B part of one chunk, by 512 threads: column exponents F (to F_out[64])
+// and the S digit planes (to planes, in the core-matrix layout the MMA reads).
+// A column's kc values are split over kc / 8 neighbouring lanes, each with 8
+// consecutive k values: its column maximum by shuffles among them, and each
+// plane's 8 digits of one column form one 16-byte core-matrix row, written
+// with one store.  Used by the pre-pass, which writes to global memory; the
+// digits come from the same function as the in-kernel slicing, so they are
+// the same whichever runs.
 template <bool FP16, int S>
 __device__ __forceinline__ void slice_b_chunk(const DevDesc& d, int n0, int k0, int warp, int lane,
                                               uint8_t* planes, int* F_out) {
     using C_ = Cfg<FP16, S>;
-    constexpr int BETA = C_::beta, KC = C_::kc, KB = KC / 32;
+    constexpr int BETA = C_::beta, KC = C_::kc;
+    constexpr int LPC = KC / 8;        // lanes per column
+    constexpr int CPW = 32 / LPC;      // columns per warp
+    if (warp >= kTN / CPW) return;     // FP16 (kc 32): half the warps cover the 64 columns
+    const int j = warp * CPW + lane / LPC, sub = lane % LPC;
     const int kcl = min(KC, d.k - k0);
     const int wc = min(kTN, d.n - n0);
+    double bv[8];
+    unsigned long long mx = 0;
+    const double* bp = d.B + (size_t)(k0 + 8 * sub) + (size_t)(n0 + j) * (size_t)d.ldb;
 #pragma unroll
-    for (int jc = 0; jc < 4; ++jc) {
-        const int j = 4 * warp + jc;
-        double bv[KB];
-        unsigned long long mx = 0;
-#pragma unroll
-        for (int h = 0; h < KB; ++h) {
-            const int kk = lane + 32 * h;
-            bv[h] = (j < wc && kk < kcl) ? __ldg(d.B + (size_t)(k0 + kk) + (size_t)(n0 + j) * (size_t)d.ldb) : 0.0;
-            const unsigned long long v = (unsigned long long)__double_as_longlong(bv[h]) & 0x7FFFFFFFFFFFFFFFull;
-            mx = v > mx ? v : mx;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long w = __shfl_xor_sync(0xffffffffu, mx, o);
-            mx = w > mx ? w : mx;
-        }
-        const int F = mx ? exp_of_bits(mx) : 0;
-        if (lane == 0) F_out[j] = F;
-        uint8_t* dst = planes + (j >> 3) * C_::sbo + (j & 7) * 16;
-#pragma unroll
-        for (int h = 0; h < KB; ++h) {
-            const int kk = lane + 32 * h;
-            int dg[S];
-            make_digits<S, BETA>(bv[h], F, dg);
-#pragma unroll
-            for (int s2 = 0; s2 < S; ++s2)
-                *reinterpret_cast<uint16_t*>(dst + s2 * C_::planeB + (kk >> 3) * 128 + (kk & 7) * 2) =
-                    digit_bits<FP16>(dg[s2]);
-        }
+    for (int i = 0; i < 8; ++i) {
+        bv[i] = (j < wc && 8 * sub + i < kcl) ? __ldg(bp + i) : 0.0;
+        const unsigned long long v = (unsigned long long)__double_as_longlong(bv[i]) & 0x7FFFFFFFFFFFFFFFull;
+        mx = v > mx ? v : mx;
     }
+#pragma unroll
+    for (int o = LPC / 2; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = w > mx ? w : mx;
+    }
+    const int F = mx ? exp_of_bits(mx) : 0;
+    if (sub == 0) F_out[j] = F;
+    uint32_t packed[S][4];
+#pragma unroll
+    for (int p = 0; p < 8; p += 2) {
+        int d0[S], d1[S];
+        make_digits<S, BETA>(bv[p], F, d0);
+        make_digits<S, BETA>(bv[p + 1], F, d1);
+#pragma unroll
+        for (int s2 = 0; s2 < S; ++s2)
+            packed[s2][p >> 1] = (uint32_t)digit_bits<FP16>(d0[s2]) | ((uint32_t)digit_bits<FP16>(d1[s2]) << 16);
+    }
+    uint8_t* dst = planes + (j >> 3) * C_::sbo + (j & 7) * 16 + sub * 128;
+#pragma unroll
+    for (int s2 = 0; s2 < S; ++s2)
+        *reinterpret_cast<uint4*>(dst + s2 * C_::planeB) =
+            make_uint4(packed[s2][0], packed[s2][1], packed[s2][2], packed[s2][3]);
 }
 
-// Pre-pass: one 512-thread CTA per B unit (entry, 64-column tile, k-chunk).
+// Pre-pass: one 512-thread CTA per B unit (entry, 64-column tile, k-chunk);
+// at most 40 registers, so three CTAs share an SM (measured: as fast or
+// faster than two at 46 registers).
 // Every 128-row tile of an entry uses the same B chunks; slicing them once
 // here instead of once per row tile removes the repeated integer work.
 template <bool FP16, int S>
-__global__ void __launch_bounds__(kThreadsS) k_slice_b(const DevDesc* __restrict__ descs,
+__global__ void __launch_bounds__(kThreadsS, 3) k_slice_b(const DevDesc* __restrict__ descs,
                                                        const BUnit* __restrict__ units, uint8_t* __restrict__ out) {
     using C_ = Cfg<FP16, S>;
     const BUnit u = units[blockIdx.x];
