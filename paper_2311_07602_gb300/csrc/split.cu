@@ -360,14 +360,45 @@ __device__ __forceinline__ void slice_b_chunk(const DevDesc& d, int n0, int k0, 
     const int F = mx ? exp_of_bits(mx) : 0;
     if (sub == 0) F_out[j] = F;
     uint32_t packed[S][4];
+    bool fast = false;
+    if constexpr (!FP16 && S == 3) {
+        // the 32-bit digit path of the in-kernel slicing of A, for a column
+        // whose key (largest high word, bit 0 set when any low word is
+        // nonzero; the same over the column's lanes) allows it: the same
+        // digits as the 64-bit path, in fewer instructions
+        uint32_t key = 0, lo = 0;
 #pragma unroll
-    for (int p = 0; p < 8; p += 2) {
-        int d0[S], d1[S];
-        make_digits<S, BETA>(bv[p], F, d0);
-        make_digits<S, BETA>(bv[p + 1], F, d1);
+        for (int i = 0; i < 8; ++i) {
+            const unsigned long long bb = (unsigned long long)__double_as_longlong(bv[i]);
+            key = max(key, (uint32_t)(bb >> 32) & 0x7FFFFFFFu);
+            lo |= (uint32_t)bb;
+        }
+        key |= lo != 0u ? 1u : 0u;
 #pragma unroll
-        for (int s2 = 0; s2 < S; ++s2)
-            packed[s2][p >> 1] = (uint32_t)digit_bits<FP16>(d0[s2]) | ((uint32_t)digit_bits<FP16>(d1[s2]) << 16);
+        for (int o = LPC / 2; o > 0; o >>= 1) key = max(key, __shfl_xor_sync(0xffffffffu, key, o));
+        fast = key_fast(key);
+        if (fast) {
+            const int ksh = key_shift(key);
+#pragma unroll
+            for (int p = 0; p < 8; p += 2) {
+                float2 f1, f2, f3;
+                digits_bf16_s3_x2(bv[p], bv[p + 1], ksh, f1, f2, f3);
+                packed[0][p >> 1] = __byte_perm(__float_as_uint(f1.x), __float_as_uint(f1.y), 0x7632);
+                packed[1][p >> 1] = __byte_perm(__float_as_uint(f2.x), __float_as_uint(f2.y), 0x7632);
+                packed[2][p >> 1] = __byte_perm(__float_as_uint(f3.x), __float_as_uint(f3.y), 0x7632);
+            }
+        }
+    }
+    if (!fast) {
+#pragma unroll
+        for (int p = 0; p < 8; p += 2) {
+            int d0[S], d1[S];
+            make_digits<S, BETA>(bv[p], F, d0);
+            make_digits<S, BETA>(bv[p + 1], F, d1);
+#pragma unroll
+            for (int s2 = 0; s2 < S; ++s2)
+                packed[s2][p >> 1] = (uint32_t)digit_bits<FP16>(d0[s2]) | ((uint32_t)digit_bits<FP16>(d1[s2]) << 16);
+        }
     }
     uint8_t* dst = planes + (j >> 3) * C_::sbo + (j & 7) * 16 + sub * 128;
 #pragma unroll
@@ -403,6 +434,7 @@ __global__ void __launch_bounds__(kThreadsS) k_slice_a(const DevDesc* __restrict
     using C_ = Cfg<FP16, S>;
     constexpr int BETA = C_::beta, KC = C_::kc, QC = KC / 4;
     __shared__ unsigned long long s_rmax[4][kTM];
+    __shared__ uint32_t s_rkey[4][kTM];
     const BUnit u = units[blockIdx.x];
     const DevDesc d = descs[u.entry];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -427,24 +459,57 @@ __global__ void __launch_bounds__(kThreadsS) k_slice_a(const DevDesc* __restrict
         mx = v > mx ? v : mx;
     }
     s_rmax[q][rloc] = mx;
+    constexpr bool KEYED = !FP16 && S == 3;   // the 32-bit digit path, as in the kernel's own slicing
+    if constexpr (KEYED) {
+        uint32_t hmx = 0, lo = 0;
+#pragma unroll
+        for (int p = 0; p < QC; ++p) {
+            const unsigned long long bb = (unsigned long long)__double_as_longlong(av[p]);
+            hmx = max(hmx, (uint32_t)(bb >> 32) & 0x7FFFFFFFu);
+            lo |= (uint32_t)bb;
+        }
+        s_rkey[q][rloc] = hmx | (lo != 0u ? 1u : 0u);
+    }
     __syncthreads();
     mx = s_rmax[0][rloc];
 #pragma unroll
     for (int qq = 1; qq < 4; ++qq) mx = s_rmax[qq][rloc] > mx ? s_rmax[qq][rloc] : mx;
     const int E = mx ? exp_of_bits(mx) : 0;
     if (q == 0) reinterpret_cast<int*>(dst0 + S * C_::planeA)[rloc] = E;
+    // a row whose key allows it (the same for the row's four quarters) takes the
+    // 32-bit digit path: the same digits in fewer instructions
+    bool fast = false;
+    int ksh = 0;
+    if constexpr (KEYED) {
+        const uint32_t key = max(max(s_rkey[0][rloc], s_rkey[1][rloc]), max(s_rkey[2][rloc], s_rkey[3][rloc]));
+        fast = key_fast(key);
+        ksh = key_shift(key);
+    }
     uint8_t* dst = dst0 + (rloc >> 3) * C_::sbo + (rloc & 7) * 16 + (q * QC / 8) * 128;
 #pragma unroll
     for (int g = 0; g < QC / 8; ++g) {
         uint32_t packed[S][4];
+        if (fast) {
+            if constexpr (KEYED) {
 #pragma unroll
-        for (int p = 0; p < 8; p += 2) {
-            int d0[S], d1[S];
-            make_digits<S, BETA>(av[8 * g + p], E, d0);
-            make_digits<S, BETA>(av[8 * g + p + 1], E, d1);
+                for (int p = 0; p < 8; p += 2) {
+                    float2 f1, f2, f3;
+                    digits_bf16_s3_x2(av[8 * g + p], av[8 * g + p + 1], ksh, f1, f2, f3);
+                    packed[0][p >> 1] = __byte_perm(__float_as_uint(f1.x), __float_as_uint(f1.y), 0x7632);
+                    packed[1][p >> 1] = __byte_perm(__float_as_uint(f2.x), __float_as_uint(f2.y), 0x7632);
+                    packed[2][p >> 1] = __byte_perm(__float_as_uint(f3.x), __float_as_uint(f3.y), 0x7632);
+                }
+            }
+        } else {
 #pragma unroll
-            for (int s2 = 0; s2 < S; ++s2)
-                packed[s2][p >> 1] = (uint32_t)digit_bits<FP16>(d0[s2]) | ((uint32_t)digit_bits<FP16>(d1[s2]) << 16);
+            for (int p = 0; p < 8; p += 2) {
+                int d0[S], d1[S];
+                make_digits<S, BETA>(av[8 * g + p], E, d0);
+                make_digits<S, BETA>(av[8 * g + p + 1], E, d1);
+#pragma unroll
+                for (int s2 = 0; s2 < S; ++s2)
+                    packed[s2][p >> 1] = (uint32_t)digit_bits<FP16>(d0[s2]) | ((uint32_t)digit_bits<FP16>(d1[s2]) << 16);
+            }
         }
 #pragma unroll
         for (int s2 = 0; s2 < S; ++s2)

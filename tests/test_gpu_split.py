@@ -66,9 +66,29 @@ def plant_special_rows(b, p):
     A[5, kc + 7] = 5e-324
     E = 3                                   # ties: (Z + 1/2) 2^(E - beta S) with |values| < 2^E
     Z = np.arange(1, 40) * 977
+    A[9, :] = 0.0                           # nothing else in the row, so the chunk maximum is the one below
     A[9, :len(Z)] = np.ldexp(Z + 0.5, E - p.beta * p.S)
     A[9, 50] = np.ldexp(1.0, E) * (1 - 2.0 ** -40)
     A[11, :] = np.ldexp(1.0 - 2.0 ** -53, 2) * np.sign(np.random.default_rng(2).standard_normal(A.shape[1]))
+    return b
+
+
+def plant_special_cols(b, p):
+    """The same cases in columns of B, which the pre-pass slices column by
+    column: a zero column, a column of values below 2^-997 in one chunk only
+    (one subnormal), exact half-unit ties, and a column maximum just below a
+    power of two."""
+    B = entry_view(b.B.numpy(), int(b.offB[0]), int(b.k[0]), int(b.n[0]), int(b.ldb[0]))
+    kc = p.kc
+    B[:, 3] = 0.0
+    B[kc:2 * kc, 5] = np.random.default_rng(3).standard_normal(kc) * 1e-305
+    B[kc + 7, 5] = 5e-324
+    E = 3
+    Z = np.arange(1, 40) * 613
+    B[:, 9] = 0.0
+    B[:len(Z), 9] = np.ldexp(Z + 0.5, E - p.beta * p.S)
+    B[50, 9] = np.ldexp(1.0, E) * (1 - 2.0 ** -40)
+    B[:, 11] = np.ldexp(1.0 - 2.0 ** -53, 2) * np.sign(np.random.default_rng(4).standard_normal(B.shape[0]))
     return b
 
 
@@ -76,10 +96,11 @@ def plant_special_rows(b, p):
 @pytest.mark.parametrize("n", [70, 40])
 def test_level_sums_bitwise(handle, name, n):
     # n = 70: several column tiles, both operands sliced by the pre-passes;
-    # n = 40: one column tile, A sliced inside the kernel (the 32-bit digit
-    # path for BF16 S = 3, with the special rows below)
+    # n = 40: one column tile, A sliced inside the kernel; B always by the
+    # pre-pass (the 32-bit digit path for BF16 S = 3 wherever a row or column
+    # allows it, with the special rows and columns below)
     p = PRESETS[name]
-    b = plant_special_rows(wide(ragged_batch([(150, n, 2 * p.kc + 44)], pad=2, seed=7)), p)
+    b = plant_special_cols(plant_special_rows(wide(ragged_batch([(150, n, 2 * p.kc + 44)], pad=2, seed=7)), p), p)
     Ah, Bh, C0 = host(b.A), host(b.B), host(b.C)
     A, B, _ = mats(b, 0, Ah, Bh, C0)
     m, n, k = A.shape[0], B.shape[1], A.shape[1]
