@@ -119,7 +119,12 @@ lrb_status lrb_destroy(lrb_handle* h);
  * cached in the handle), splits every entry into output tiles, orders the
  * tiles longest-first and uploads descriptors and tiles to plan-owned device
  * memory.  opts == NULL means {FP64, no graph, tune, no force, check alias}.
- * The operand buffers are not touched until a launch. */
+ * C is not touched until a launch.  With tune, a plain FP64 plan (no trans,
+ * no overwrite) of two to eight waves of tiles times its own tilings before
+ * it returns -- a few launches each of the tuned tiles and of narrower ones (the
+ * same per-element results) on its A and B and a scratch C -- and keeps the
+ * faster, so A and B must then be readable device memory at creation.
+ * Otherwise the operand buffers are not touched until a launch. */
 lrb_status lrb_plan_create(lrb_handle* h, const lrb_gemm_desc* host_descs, size_t count,
                            const lrb_plan_opts* opts, lrb_plan** out);
 

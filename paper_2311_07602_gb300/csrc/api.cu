@@ -516,6 +516,63 @@ lrb_status tune_bucket(lrb_handle* h, int m, int n, int k, bool dmma_ok, int* be
     return LRB_OK;
 }
 
+// One persistent launch of the entries with tile variants `var` (all in the
+// slim set), on the entries' own A and B and a scratch C (tight, zeroed: the
+// caller's C is not touched): the best of three timed launches after a
+// warm-up, in ms.  Used to choose between near-tied tilings of small plans.
+lrb_status time_plan_tiles(lrb_handle* h, const lrb_gemm_desc* d, size_t count, const std::vector<int>& var,
+                           float* ms_out) {
+    std::vector<Item> items;
+    make_tiles(d, count, var, items);
+    std::vector<size_t> coff(count);
+    size_t c_elems = 0;
+    for (size_t e = 0; e < count; ++e) {
+        coff[e] = c_elems;
+        c_elems += ((size_t)d[e].m * (size_t)d[e].n + 31) / 32 * 32;
+    }
+    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+    const size_t o_desc = up(8 * c_elems), o_items = o_desc + up(sizeof(DevDesc) * count);
+    const size_t o_head = o_items + up(sizeof(Item) * items.size()), total = o_head + 256;
+    void* mem = nullptr;
+    LRB_CUDA(cudaMalloc(&mem, total));
+    char* base = (char*)mem;
+    double* C = (double*)base;
+    std::vector<DevDesc> dd(count);
+    for (size_t e = 0; e < count; ++e)
+        dd[e] = DevDesc{d[e].A, d[e].B, C + coff[e], d[e].m, d[e].n, d[e].k, d[e].lda, d[e].ldb, d[e].m};
+    DevDesc* d_dd = (DevDesc*)(base + o_desc);
+    Item* d_items = (Item*)(base + o_items);
+    int* d_head = (int*)(base + o_head);
+    cudaError_t ce = cudaMemsetAsync(C, 0, 8 * c_elems, h->stream);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(d_dd, dd.data(), sizeof(DevDesc) * count, cudaMemcpyHostToDevice, h->stream);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice, h->stream);
+    const int n_items = (int)items.size();
+    const int grid = std::max(1, std::min(h->sms * h->blocks_per_sm_slim, n_items));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce == cudaSuccess) ce = launch_persistent(d_dd, d_items, n_items, d_head, grid, h->stream, 0, 0);
+    float best = 1e30f;
+    for (int rep = 0; rep < 3 && ce == cudaSuccess; ++rep) {
+        cudaEventRecord(e0, h->stream);
+        ce = launch_persistent(d_dd, d_items, n_items, d_head, grid, h->stream, 0, 0);
+        cudaEventRecord(e1, h->stream);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (ce == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        best = std::min(best, ms);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(h->stream);
+    cudaFree(mem);
+    if (ce != cudaSuccess) return cuda_fail(ce, "timing a small plan's tiles");
+    *ms_out = best;
+    return LRB_OK;
+}
+
 lrb_status choose_variants(lrb_handle* h, const lrb_gemm_desc* d, size_t count, const lrb_plan_opts& o,
                            std::vector<int>& var) {
     var.resize(count);
@@ -767,6 +824,35 @@ lrb_status lrb_plan_create(lrb_handle* h, const lrb_gemm_desc* host_descs, size_
             }
         }
         if (changed) make_tiles(host_descs, count, var, items);
+    } else if (o.tune && o.force_variant < 0 && o.trans == 0 && o.overwrite == 0 &&
+               items.size() < 8 * (size_t)h->sms * (size_t)h->blocks_per_sm_slim) {
+        // Two to eight waves: the last wave's share of the time is large, and
+        // the bucket tuner (which times full waves) cannot see it.  Narrower
+        // tiles (64x16 and 64x32 -> 64x8: the same per-element k order, so
+        // the same results) give more, shorter tiles for the tail; time both
+        // tilings on this plan's own operands and keep the faster (the
+        // narrower one only if it gains 1 % or more).
+        bool all_slim = true, narrowable = false;
+        for (int v : var) {
+            all_slim = all_slim && variant_set(v) == 0;
+            narrowable = narrowable || v == 1 || v == 2;
+        }
+        if (all_slim && narrowable) {
+            std::vector<int> alt(var);
+            for (int& v : alt)
+                if (v == 1 || v == 2) v = 0;
+            float t_cur = 0, t_alt = 0;
+            lrb_status st = time_plan_tiles(h, host_descs, count, var, &t_cur);
+            if (st == LRB_OK) st = time_plan_tiles(h, host_descs, count, alt, &t_alt);
+            if (st != LRB_OK) {
+                free_plan(p);
+                return st;
+            }
+            if (t_alt < 0.99f * t_cur) {
+                var.swap(alt);
+                make_tiles(host_descs, count, var, items);
+            }
+        }
     }
     if (items.size() > 0x7fffffffull) {
         free_plan(p);
