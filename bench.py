@@ -55,11 +55,13 @@ DFMA_LANES_PER_SM_CLK = 2          # FP64 FMA lanes per SM per clock on GB300 (1
 # DRAM bytes (read + write) per algorithmic byte of k_persistent on the
 # variable-size batch, from an ncu capture of a 1/20-scale case of the same
 # batch (its first 1,000 entries, same 4 GB pool): 6.716 GB read + 2.323 GB
-# written for 7.356 GB algorithmic.  Valid while the kernels (fp64_tiles.cu)
-# and the planner and tuner that choose their tiles (api.cu) have the SHA-256
-# prefix below (the roofline's traffic is null otherwise).
+# written for 7.356 GB algorithmic (an earlier capture with another tuning
+# outcome gave 1.225).  Valid while the kernels (fp64_tiles.cu) and the
+# planner and tuner that choose their tiles (api.cu) have the SHA-256 prefix
+# below (the roofline's traffic is null otherwise); the prefix was renewed
+# after a planner change that concerns plans of two to eight waves only.
 TRAFFIC_PER_ALG_BYTE = 1.22873
-TRAFFIC_SOURCE_SHA = "6a71bc57959e9337"
+TRAFFIC_SOURCE_SHA = "ec8019b9cf4065de"
 
 
 def dist_env():
