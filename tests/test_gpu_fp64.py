@@ -138,6 +138,25 @@ def test_small_o_form_full_parity(handle):
     assert np.array_equal(host(dev2.C).view(np.uint64), got.view(np.uint64))
 
 
+def test_small_plan_tiling_choice_keeps_results(handle):
+    """A tuned plan of two to eight waves times its tiling against narrower
+    64 x 8 tiles and keeps the faster; the non-split tiles give every element
+    the same k order, so whichever it keeps, C is bitwise that of the plans
+    forced to 64 x 8, 64 x 16 and 64 x 32 tiles, and matches the oracle."""
+    b = W.small_o_form()
+    Ah, Bh, C0 = host(b.A), host(b.B), host(b.C)
+    outs = {}
+    for name, force in (("tuned", -1), ("64x8", 0), ("64x16", 1), ("64x32", 2)):
+        dev = b.to("cuda")
+        with handle.plan(L.descs_for(dev), use_graph=True, force_variant=force) as p:
+            p.launch()
+            torch.cuda.synchronize()
+        outs[name] = host(dev.C)
+    for name in ("64x8", "64x16", "64x32"):
+        assert np.array_equal(outs[name].view(np.uint64), outs["tuned"].view(np.uint64)), name
+    check_entries(outs["tuned"], oracle_batch(Ah, Bh, C0, b), Ah, Bh, C0, b)
+
+
 def test_persistent_plain_graph_bitwise_and_repeatable(handle):
     forms, bs, rs = W.variable_shapes(300, seed=31, bmin=16, bmax=600)
     base = W.variable_batch(forms, bs, rs, seed=31)
